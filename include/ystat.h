@@ -1,0 +1,175 @@
+/*
+ * ystat -- power-spectrum multipoles P_0, P_2, P_4 of a galaxy survey with a varying
+ * line of sight, by the FFT-based Yamamoto estimator of Bianchi, Gil-Marin, Ruggeri &
+ * Percival (2015), on one NVIDIA GB300 (sm_103a).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   Eq. (1)       F(r) = w(r) [n(r) - alpha n_s(r)] / I^(1/2)     -> ys_assign
+ *   Eqs. (4)-(13) P_l(k) from A_0, B_ij, C_ijl via FFTs             -> ys_measure_multipoles
+ * All arithmetic runs in the CUDA kernels of this library; there is no CPU fallback.
+ * A call that needs the GPU fails with YS_ERR_CUDA when no usable device is present.
+ *
+ * Conventions shared by every call
+ *  - Positions are comoving Cartesian coordinates (Mpc/h), float32, structure of
+ *    arrays.  The analysis box is the cube [box_min, box_min + box_len)^3, divided into
+ *    n_mesh^3 cells of side H = box_len / n_mesh; mesh node i sits at box_min + i H
+ *    (the interlaced mesh at box_min + (i + 1/2) H).  The box is periodic.
+ *  - Pointers named d_* are device pointers, h_* host pointers.  The caller owns every
+ *    buffer it passes; no call keeps a caller pointer after it returns.
+ *  - Work is queued on the plan's CUDA stream and is asynchronous unless a call says
+ *    otherwise.  Calls on one plan must not overlap.
+ *  - Every call returns a ys_status and never aborts the process.
+ */
+#ifndef YSTAT_H
+#define YSTAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  YS_OK = 0,
+  YS_ERR_ARG = 1,          /* invalid argument, or particles outside the box   */
+  YS_ERR_OOM = 2,          /* device allocation failed                          */
+  YS_ERR_CUDA = 3,         /* CUDA runtime error (see ys_last_cuda_error)       */
+  YS_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out                */
+  YS_ERR_UNSUPPORTED = 5,  /* mesh size or option this build does not handle   */
+  YS_ERR_STATE = 6         /* call out of order (e.g. measure before assign)    */
+} ys_status;
+
+typedef enum { YS_NGP = 1, YS_CIC = 2, YS_TSC = 3 } ys_assign_kind;
+
+/* Estimator configuration.
+ *  n_mesh     N: 16 <= N <= 1024, N = 2^a or 3 * 2^a (a >= 4 for the latter).
+ *  box_min, box_len, observer   geometry; r = node - observer is the line of sight
+ *             used for the LOS weights of Eqs. (11) and (13) (weight 0 at r = 0).
+ *  assign     NGP / CIC / TSC particle-to-mesh kernel (Sec. 4 uses CIC).
+ *  interlace  1: a second mesh shifted by H/2 on every axis; the two transforms are
+ *             averaged with the phase e^{-i k.(H/2)(1,1,1)}.
+ *  compensate 1: divide every A_n(k) by prod_i sinc(k_i H / 2)^p, p = 1, 2, 3.
+ *  ell_max    0, 2 or 4: highest multipole; 1, 7 or 22 fields of Sec. 3.
+ *  k_min, dk, n_bins   shells [k_min + b dk, k_min + (b+1) dk), b < n_bins <= 4096; only
+ *             modes with 0 < |k| < k_Nyquist = pi N / box_len enter.
+ *  alpha      < 0: alpha = sum_gal w / sum_ran w (Eq. 1); else this value.
+ *  max_particles   capacity (galaxies + randoms) of the plan's particle buffers.
+ *  stream     cudaStream_t to queue work on (NULL = legacy default stream). */
+typedef struct {
+  int32_t n_mesh;
+  double box_min[3];
+  double box_len;
+  double observer[3];
+  int32_t assign;
+  int32_t interlace;
+  int32_t compensate;
+  int32_t ell_max;
+  double k_min;
+  double dk;
+  int32_t n_bins;
+  double alpha;
+  int64_t max_particles;
+  void* stream;
+} ys_config;
+
+/* A catalogue: n particles, float32 arrays of length n.
+ * w    NULL = unit weights.  nbar: expected galaxy density at each position (Eq. 1),
+ * used for the normalisation I (randoms only); NULL = not given (I is then 0 and
+ * P_l are NaN).  Device pointers for ys_assign, host pointers for ys_estimate_host. */
+typedef struct {
+  const float* x;
+  const float* y;
+  const float* z;
+  const float* w;
+  const float* nbar;
+  int64_t n;
+} ys_catalog;
+
+/* Host-side result of one measurement (arrays of length n_bins, caller-owned).
+ * k_mean  mean |k| of the modes in the shell (h/Mpc); n_modes  number of modes (full
+ * k-space count); p0, p2, p4  the multipoles of Eqs. (6)-(8) in (Mpc/h)^3 with the
+ * shot noise S/I subtracted from p0 only (Eq. 3).  Empty shells give NaN and
+ * n_modes = 0.  Any array pointer may be NULL.  alpha, norm_I = alpha sum_ran w^2 nbar,
+ * shot_noise = S / I with S = sum_gal w^2 + alpha^2 sum_ran w^2 are filled in. */
+typedef struct {
+  double* k_mean;
+  double* n_modes;
+  double* p0;
+  double* p2;
+  double* p4;
+  double alpha;
+  double norm_I;
+  double shot_noise;
+} ys_result;
+
+typedef struct ys_plan_s ys_plan;
+
+/* Validate cfg and create a plan: allocates the meshes, the transformed fields,
+ * the shell tables and the particle buffers on the current device (cudaMalloc);
+ * the plan owns and frees them.  Host-side; may synchronise the device. */
+ys_status ys_plan_create(const ys_config* cfg, ys_plan** out);
+
+/* Device bytes the plan holds (0 if plan is NULL). */
+size_t ys_plan_device_bytes(const ys_plan* plan);
+
+/* Eq. (1): deposit galaxies (+w) and randoms (-alpha w) onto the mesh(es), and
+ * accumulate the FP64 catalogue sums behind alpha, I and S.  gal/ran hold DEVICE
+ * pointers.  Asynchronous.  Particles outside the box are wrapped periodically and
+ * reported by the next ys_measure_multipoles as YS_ERR_ARG. */
+ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran);
+
+/* Eqs. (4)-(13): the LOS-weighted fields, their FFTs, the k-space combination,
+ * the shell sums and Eqs. (6)-(8).  Writes the device result row
+ *   d_out[0 .. 5 n_bins + 3) = [k_mean | n_modes | p0 | p2 | p4 | alpha, I, S/I]
+ * (doubles) asynchronously.  d_out may be NULL (the plan keeps its own copy). */
+ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out);
+
+/* As ys_measure_multipoles_async, then waits for the stream and copies the result
+ * into the caller's host arrays.  Returns YS_ERR_ARG if ys_assign saw particles
+ * outside the box (results are still written). */
+ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out);
+
+/* End-to-end convenience: gal/ran hold HOST pointers (pinned or pageable); copies them
+ * to plan-owned device buffers, runs ys_assign and ys_measure_multipoles, and fills
+ * the host result.  Synchronous. */
+ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran,
+                           ys_result* out);
+
+/* Per-kernel statistics (measurement support; no counterpart in the paper).
+ * With profiling on, every kernel launch of the plan is bracketed by CUDA events on
+ * the plan's stream and ys_measure_multipoles* launches directly instead of
+ * replaying its captured CUDA graph.  Kernel classes, in order:
+ *   0 particle count + catalogue sums, 1 tile scan, 2 particle binning,
+ *   3 tile deposit, 4 y,z-stage rows (fields + FFT along z), 5 y,z-stage columns
+ *   (FFT along y + k_x-power grouping), 6 x-stage (FFT along x + combine + shells),
+ *   7 finalize.
+ * launches[c] counts kernel launches of class c, ms[c] their summed device time
+ * (valid only for launches made while profiling was on). */
+#define YS_NUM_KERNEL_CLASSES 8
+typedef struct {
+  int64_t launches[YS_NUM_KERNEL_CLASSES];
+  double ms[YS_NUM_KERNEL_CLASSES];
+} ys_stats;
+
+/* enable != 0 turns event profiling on.  Host-side. */
+ys_status ys_plan_set_profiling(ys_plan* plan, int enable);
+
+/* Waits for the plan's stream, then fills *out with the counts and times since the
+ * last reset; reset != 0 clears them afterwards. */
+ys_status ys_plan_get_stats(ys_plan* plan, ys_stats* out, int reset);
+
+/* Free everything the plan owns.  NULL is accepted. */
+ys_status ys_plan_destroy(ys_plan* plan);
+
+/* Static description of a status code. */
+const char* ys_status_string(ys_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* ys_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YSTAT_H */

@@ -1,0 +1,532 @@
+// C ABI of the ystat library: plan creation (validation, FP64 host tables, device
+// allocation), the assign / measure entry points, and the final Eqs. (6)-(8).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ys_internal.h"
+
+namespace ys {
+
+template <int N> cudaError_t run_measure_n(Plan& p);
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+ys_status cuda_fail(cudaError_t e) {
+  g_last_cuda_error = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? YS_ERR_OOM : YS_ERR_CUDA;
+}
+
+bool supported_n(int n) {
+  static const int ok[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+  for (int v : ok)
+    if (v == n) return true;
+  return false;
+}
+
+template <class T>
+cudaError_t dalloc(Plan& p, T*& ptr, size_t count) {
+  void* raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, count * sizeof(T) + 16);
+  if (e == cudaSuccess) {
+    ptr = static_cast<T*>(raw);
+    p.device_bytes += count * sizeof(T) + 16;
+  }
+  return e;
+}
+
+template <class T>
+void dfree(T*& ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+void free_all(Plan& p) {
+  dfree(p.d_tw); dfree(p.d_nodes); dfree(p.d_rel); dfree(p.d_invw); dfree(p.d_phase);
+  dfree(p.d_col_off); dfree(p.d_pencil); dfree(p.d_lut); dfree(p.d_shell);
+  dfree(p.d_mesh); dfree(p.d_z); dfree(p.d_g); dfree(p.d_acc); dfree(p.d_sums); dfree(p.d_result);
+  dfree(p.d_tile_count); dfree(p.d_tile_off); dfree(p.d_tile_cur); dfree(p.d_rec); dfree(p.d_rec_cell);
+  dfree(p.d_stage);
+  p.device_bytes = 0;
+}
+
+__global__ void k_finalize(const double* __restrict__ acc, const double* __restrict__ shell,
+                           const double* __restrict__ sums, double alpha_cfg, int nbins, int ell,
+                           double* __restrict__ res) {
+  const double alpha = alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR];
+  const double I = alpha * sums[SUM_WR2N];
+  const double S = sums[SUM_WG2] + alpha * alpha * sums[SUM_WR2];
+  const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    const double nm = shell[b];
+    double km = nan, p0 = nan, p2 = nan, p4 = nan;
+    if (nm > 0.0) {
+      km = shell[nbins + b] / nm;
+      const double m0 = acc[b] / nm, m2 = acc[nbins + b] / nm, m4 = acc[2 * nbins + b] / nm;
+      // Eqs. (6)-(8), shot noise subtracted from the monopole only (Eq. 3).
+      p0 = (m0 - S) / I;
+      if (ell >= 2) p2 = 2.5 / I * (3.0 * m2 - m0);
+      if (ell >= 4) p4 = 1.125 / I * (35.0 * m4 - 30.0 * m2 + 3.0 * m0);
+    }
+    res[b] = km;
+    res[nbins + b] = nm;
+    res[2 * nbins + b] = p0;
+    res[3 * nbins + b] = p2;
+    res[4 * nbins + b] = p4;
+  }
+  if (threadIdx.x == 0) {
+    res[5 * nbins + 0] = alpha;
+    res[5 * nbins + 1] = I;
+    res[5 * nbins + 2] = S / I;
+    res[5 * nbins + 3] = sums[SUM_BAD];
+  }
+}
+
+// FP64 host tables (shells, pencils, windows, phases, twiddles, node positions).
+ys_status build_tables(Plan& p) {
+  const ys_config& c = p.cfg;
+  const int n = p.n;
+  const double L = c.box_len;
+  p.H = L / n;
+  p.kf = 2.0 * M_PI / L;
+  const double knyq = p.kf * n / 2.0;
+  // shell index per integer |m|^2 (only |m|^2 < (n/2)^2 can satisfy |k| < k_Nyquist)
+  const int n2max = (n / 2) * (n / 2);
+  std::vector<short> lut(n2max, -1);
+  int n2_hi = 0;
+  for (int n2 = 1; n2 < n2max; ++n2) {
+    const double kmag = p.kf * std::sqrt((double)n2);
+    if (!(kmag < knyq)) continue;
+    const double b = std::floor((kmag - c.k_min) / c.dk);
+    if (b >= 0 && b < c.n_bins) {
+      lut[n2] = (short)b;
+      n2_hi = n2 + 1;
+    }
+  }
+  p.n2_hi = n2_hi;
+  // pencils (k_y, k_z), k_z >= 0, k_y^2 + k_z^2 < n2_hi; column k_z holds |k_y| <= kymax
+  std::vector<int> col_off;
+  std::vector<short2> pen;
+  int nzc = 0;
+  while (n2_hi > 0 && nzc * nzc < n2_hi) ++nzc;
+  col_off.push_back(0);
+  for (int kz = 0; kz < nzc; ++kz) {
+    int kymax = 0;
+    while ((kymax + 1) * (kymax + 1) + kz * kz < n2_hi) ++kymax;
+    for (int ky = -kymax; ky <= kymax; ++ky) pen.push_back(make_short2((short)ky, (short)kz));
+    col_off.push_back((int)pen.size());
+  }
+  p.nzc = nzc;
+  p.np = (int)pen.size();
+  // mode count and sum |k| per shell (half grid, weight 2 for 0 < k_z < n/2)
+  std::vector<double> shell(2 * c.n_bins, 0.0);
+  for (int kz = 0; kz < nzc; ++kz) {
+    const int kymax = (col_off[kz + 1] - col_off[kz] - 1) / 2;
+    const double w = kz == 0 ? 1.0 : 2.0;
+    for (int ky = -kymax; ky <= kymax; ++ky)
+      for (int mx = -n / 2 + 1; mx < n / 2; ++mx) {
+        const int n2 = mx * mx + ky * ky + kz * kz;
+        if (n2 >= n2_hi || n2 <= 0) continue;
+        const int b = lut[n2];
+        if (b < 0) continue;
+        shell[b] += w;
+        shell[c.n_bins + b] += w * p.kf * std::sqrt((double)n2);
+      }
+  }
+  // per-axis window compensation and interlacing phase by FFT index
+  const int pw = c.assign;  // NGP 1, CIC 2, TSC 3
+  std::vector<float> invw(n);
+  std::vector<float2> phase(n), tw(n);
+  for (int i = 0; i < n; ++i) {
+    const int m = i <= n / 2 ? i : i - n;
+    const double x = M_PI * m / n;
+    double W = 1.0;
+    if (m != 0) W = std::pow(std::sin(x) / x, pw);
+    invw[i] = c.compensate ? (float)(1.0 / W) : 1.0f;
+    phase[i] = make_float2((float)std::cos(x), (float)-std::sin(x));
+    const double t = -2.0 * M_PI * i / n;
+    tw[i] = make_float2((float)std::cos(t), (float)std::sin(t));
+  }
+  // node positions (hi, lo) for i in [-1, n + 1], and node - observer per mesh
+  std::vector<float2> nodes(3 * (n + 3));
+  for (int a = 0; a < 3; ++a)
+    for (int i = -1; i <= n + 1; ++i) {
+      const double v = c.box_min[a] + i * p.H;
+      const float hi = (float)v;
+      nodes[a * (n + 3) + i + 1] = make_float2(hi, (float)(v - (double)hi));
+    }
+  std::vector<float> rel((size_t)p.m * 3 * n);
+  for (int j = 0; j < p.m; ++j)
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < n; ++i) {
+        const double s = j == 1 ? 0.5 : 0.0;
+        rel[((size_t)j * 3 + a) * n + i] = (float)(c.box_min[a] + (i + s) * p.H - c.observer[a]);
+      }
+  cudaError_t e;
+#define YS_UP(dst, vec)                                                                                 \
+  do {                                                                                                  \
+    if ((e = dalloc(p, dst, std::max<size_t>(1, vec.size())))) return cuda_fail(e);                     \
+    if (!vec.empty() &&                                                                                 \
+        (e = cudaMemcpy(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice)))         \
+      return cuda_fail(e);                                                                              \
+  } while (0)
+  YS_UP(p.d_lut, lut);
+  YS_UP(p.d_col_off, col_off);
+  YS_UP(p.d_pencil, pen);
+  YS_UP(p.d_shell, shell);
+  YS_UP(p.d_invw, invw);
+  YS_UP(p.d_phase, phase);
+  YS_UP(p.d_tw, tw);
+  YS_UP(p.d_nodes, nodes);
+  YS_UP(p.d_rel, rel);
+#undef YS_UP
+  return YS_OK;
+}
+
+ys_status ensure_particles(Plan& p, int64_t total) {
+  if (total <= p.part_cap) return YS_OK;
+  cudaError_t e;
+  if (p.d_rec) {
+    if ((e = cudaStreamSynchronize(p.stream))) return cuda_fail(e);
+    p.device_bytes -= (size_t)p.rec_cap * (sizeof(float4) + sizeof(int)) + 32;
+    dfree(p.d_rec);
+    dfree(p.d_rec_cell);
+  }
+  int factor = 1;
+  for (int a = 0; a < 3; ++a) factor *= p.geom.tiles[a] > 1 ? 2 : 1;
+  p.part_cap = total;
+  p.rec_cap = total * factor;
+  if ((e = dalloc(p, p.d_rec, (size_t)p.rec_cap))) return cuda_fail(e);
+  if ((e = dalloc(p, p.d_rec_cell, (size_t)p.rec_cap))) return cuda_fail(e);
+  return YS_OK;
+}
+
+bool catalog_ok(const ys_catalog* k) {
+  if (!k || k->n < 0) return false;
+  if (k->n > 0 && (!k->x || !k->y || !k->z)) return false;
+  return true;
+}
+
+}  // namespace
+
+LaunchScope::LaunchScope(Plan& plan, int c) : p(plan), cls(c) {
+  if (p.capturing) {
+    ++p.measure_launches[c];
+    return;
+  }
+  ++p.launches[c];
+  if (p.profiling) {
+    for (cudaEvent_t* ev : {&a, &b}) {
+      if (!p.event_pool.empty()) {
+        *ev = p.event_pool.back();
+        p.event_pool.pop_back();
+      } else if (cudaEventCreate(ev) != cudaSuccess) {
+        *ev = nullptr;
+      }
+    }
+    if (a && b) cudaEventRecord(a, p.stream);
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  if (a && b) {
+    cudaEventRecord(b, p.stream);
+    p.pending.push_back({a, b, cls});
+  }
+}
+
+cudaError_t launch_finalize(Plan& p) {
+  LaunchScope ls(p, 7);
+  k_finalize<<<1, 256, 0, p.stream>>>(p.d_acc, p.d_shell, p.d_sums, p.cfg.alpha, p.cfg.n_bins, p.ell,
+                                      p.d_result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure(Plan& p) {
+  switch (p.n) {
+    case 16: return run_measure_n<16>(p);
+    case 32: return run_measure_n<32>(p);
+    case 64: return run_measure_n<64>(p);
+    case 96: return run_measure_n<96>(p);
+    case 128: return run_measure_n<128>(p);
+    case 192: return run_measure_n<192>(p);
+    case 256: return run_measure_n<256>(p);
+    case 384: return run_measure_n<384>(p);
+    case 512: return run_measure_n<512>(p);
+    case 768: return run_measure_n<768>(p);
+    case 1024: return run_measure_n<1024>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ys
+
+using ys::Plan;
+
+extern "C" {
+
+const char* ys_status_string(ys_status s) {
+  switch (s) {
+    case YS_OK: return "ok";
+    case YS_ERR_ARG: return "invalid argument";
+    case YS_ERR_OOM: return "device allocation failed";
+    case YS_ERR_CUDA: return "CUDA error";
+    case YS_ERR_TIMEOUT: return "device wait timed out";
+    case YS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case YS_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* ys_last_cuda_error(void) { return ys::g_last_cuda_error.c_str(); }
+
+ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
+  if (!cfg || !out) return YS_ERR_ARG;
+  *out = nullptr;
+  const ys_config& c = *cfg;
+  if (!ys::supported_n(c.n_mesh)) return YS_ERR_UNSUPPORTED;
+  if (!(c.box_len > 0) || !std::isfinite(c.box_len)) return YS_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(c.box_min[a]) || !std::isfinite(c.observer[a])) return YS_ERR_ARG;
+  if (c.assign < YS_NGP || c.assign > YS_TSC) return YS_ERR_ARG;
+  if (c.interlace != 0 && c.interlace != 1) return YS_ERR_ARG;
+  if (c.compensate != 0 && c.compensate != 1) return YS_ERR_ARG;
+  if (c.ell_max != 0 && c.ell_max != 2 && c.ell_max != 4) return YS_ERR_ARG;
+  if (c.n_bins <= 0 || c.n_bins > 4096 || !(c.dk > 0) || !(c.k_min >= 0)) return YS_ERR_ARG;
+  if (c.max_particles < 0) return YS_ERR_ARG;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    ys::g_last_cuda_error = e != cudaSuccess ? cudaGetErrorString(e) : "no CUDA device";
+    return YS_ERR_CUDA;
+  }
+  ys_plan* h = new (std::nothrow) ys_plan;
+  if (!h) return YS_ERR_OOM;
+  Plan& p = h->p;
+  p.cfg = c;
+  p.stream = static_cast<cudaStream_t>(c.stream);
+  p.n = c.n_mesh;
+  p.m = c.interlace ? 2 : 1;
+  p.ell = c.ell_max;
+  p.kind = c.assign;
+  p.nb = p.ell == 0 ? 1 : (p.ell == 2 ? 7 : 16);
+  p.ng = p.ell == 0 ? 1 : (p.ell == 2 ? 4 : 9);
+  const int n = p.n;
+  ys::Geom& g = p.geom;
+  g.n = n;
+  g.inv_h = (float)(n / c.box_len);
+  const int tdef[3] = {ys::TILE_X, ys::TILE_Y, ys::TILE_Z};
+  p.ntiles = 1;
+  for (int a = 0; a < 3; ++a) {
+    g.bmin[a] = (float)c.box_min[a];
+    g.tdim[a] = std::min(tdef[a], n);
+    g.tiles[a] = n / g.tdim[a];
+    p.ntiles *= g.tiles[a];
+  }
+  ys_status st = ys::build_tables(p);
+  if (st != YS_OK) {
+    ys::free_all(p);
+    delete h;
+    return st;
+  }
+  const size_t n3 = (size_t)n * n * n;
+  const size_t plane_scratch = (size_t)p.nb * std::max(1, p.nzc) * n * sizeof(float2);
+  p.batch = (int)std::max<size_t>(1, std::min<size_t>(n, (48u << 20) / plane_scratch));
+  if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, plane_scratch / sizeof(float2) * p.batch)) ||
+      (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np))) ||
+      (e = ys::dalloc(p, p.d_acc, (size_t)3 * c.n_bins)) || (e = ys::dalloc(p, p.d_sums, (size_t)ys::SUM_COUNT)) ||
+      (e = ys::dalloc(p, p.d_result, (size_t)5 * c.n_bins + 4)) ||
+      (e = ys::dalloc(p, p.d_tile_count, (size_t)p.ntiles)) || (e = ys::dalloc(p, p.d_tile_off, (size_t)p.ntiles + 1)) ||
+      (e = ys::dalloc(p, p.d_tile_cur, (size_t)p.ntiles))) {
+    st = ys::cuda_fail(e);
+    ys::free_all(p);
+    delete h;
+    return st;
+  }
+  if (c.max_particles > 0 && (st = ys::ensure_particles(p, c.max_particles)) != YS_OK) {
+    ys::free_all(p);
+    delete h;
+    return st;
+  }
+  p.h_result.assign((size_t)5 * c.n_bins + 4, 0.0);
+  if (cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    p.cap_stream = nullptr;
+  }
+  *out = h;
+  return YS_OK;
+}
+
+size_t ys_plan_device_bytes(const ys_plan* plan) { return plan ? plan->p.device_bytes : 0; }
+
+ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran) {
+  if (!plan || !ys::catalog_ok(gal) || !ys::catalog_ok(ran)) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  ys_status st = ys::ensure_particles(p, gal->n + ran->n);
+  if (st != YS_OK) return st;
+  cudaError_t e = ys::launch_assign(p, *gal, *ran);
+  if (e) return ys::cuda_fail(e);
+  p.assigned = true;
+  return YS_OK;
+}
+
+ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out) {
+  if (!plan) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  if (!p.assigned) return YS_ERR_STATE;
+  cudaError_t e = cudaSuccess;
+  if (!p.profiling && p.cap_stream && !p.measure_exec) {
+    // Capture the measurement sequence once; every later call replays it.
+    cudaStream_t user = p.stream;
+    p.stream = p.cap_stream;
+    p.capturing = true;
+    for (int c = 0; c < YS_NUM_KERNEL_CLASSES; ++c) p.measure_launches[c] = 0;
+    e = cudaStreamBeginCapture(p.cap_stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e2 = cudaSuccess;
+    if (!e) {
+      e2 = ys::launch_measure(p);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(p.cap_stream, &graph);
+      if (!e && !e2) e = cudaGraphInstantiate(&p.measure_exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    p.capturing = false;
+    p.stream = user;
+    if (e || e2 || !p.measure_exec) {  // no graph: launch directly from now on
+      cudaGetLastError();
+      if (p.measure_exec) cudaGraphExecDestroy(p.measure_exec);
+      p.measure_exec = nullptr;
+      cudaStreamDestroy(p.cap_stream);
+      p.cap_stream = nullptr;
+    }
+    e = cudaSuccess;
+  }
+  if (!p.profiling && p.measure_exec) {
+    e = cudaGraphLaunch(p.measure_exec, p.stream);
+    if (e) return ys::cuda_fail(e);
+    for (int c = 0; c < YS_NUM_KERNEL_CLASSES; ++c) p.launches[c] += p.measure_launches[c];
+  } else {
+    e = ys::launch_measure(p);
+    if (e) return ys::cuda_fail(e);
+  }
+  if (d_out) {
+    e = cudaMemcpyAsync(d_out, p.d_result, sizeof(double) * (5 * p.cfg.n_bins + 4), cudaMemcpyDeviceToDevice,
+                        p.stream);
+    if (e) return ys::cuda_fail(e);
+  }
+  return YS_OK;
+}
+
+ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out) {
+  if (!plan || !out) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  ys_status st = ys_measure_multipoles_async(plan, nullptr);
+  if (st != YS_OK) return st;
+  const int nb = p.cfg.n_bins;
+  cudaError_t e = cudaMemcpyAsync(p.h_result.data(), p.d_result, sizeof(double) * (5 * nb + 4),
+                                  cudaMemcpyDeviceToHost, p.stream);
+  if (e) return ys::cuda_fail(e);
+  if ((e = cudaStreamSynchronize(p.stream))) return ys::cuda_fail(e);
+  const double* r = p.h_result.data();
+  double* dst[5] = {out->k_mean, out->n_modes, out->p0, out->p2, out->p4};
+  for (int q = 0; q < 5; ++q)
+    if (dst[q]) std::memcpy(dst[q], r + (size_t)q * nb, sizeof(double) * nb);
+  out->alpha = r[5 * nb + 0];
+  out->norm_I = r[5 * nb + 1];
+  out->shot_noise = r[5 * nb + 2];
+  return r[5 * nb + 3] > 0 ? YS_ERR_ARG : YS_OK;
+}
+
+ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran, ys_result* out) {
+  if (!plan || !ys::catalog_ok(gal) || !ys::catalog_ok(ran) || !out) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  const int64_t need = 5 * (gal->n + ran->n);
+  cudaError_t e;
+  if (need > p.stage_cap) {
+    if (p.d_stage) {
+      if ((e = cudaStreamSynchronize(p.stream))) return ys::cuda_fail(e);
+      p.device_bytes -= (size_t)p.stage_cap * sizeof(float) + 16;
+      ys::dfree(p.d_stage);
+    }
+    if ((e = ys::dalloc(p, p.d_stage, (size_t)need))) return ys::cuda_fail(e);
+    p.stage_cap = need;
+  }
+  ys_catalog dev[2];
+  const ys_catalog* src[2] = {gal, ran};
+  float* cursor = p.d_stage;
+  for (int c = 0; c < 2; ++c) {
+    const ys_catalog& s = *src[c];
+    ys_catalog& d = dev[c];
+    d.n = s.n;
+    const float* in[5] = {s.x, s.y, s.z, s.w, s.nbar};
+    const float** outp[5] = {&d.x, &d.y, &d.z, &d.w, &d.nbar};
+    for (int q = 0; q < 5; ++q) {
+      if (!in[q] || s.n == 0) {
+        *outp[q] = (q < 3) ? cursor : nullptr;
+        continue;
+      }
+      if ((e = cudaMemcpyAsync(cursor, in[q], sizeof(float) * s.n, cudaMemcpyHostToDevice, p.stream)))
+        return ys::cuda_fail(e);
+      *outp[q] = cursor;
+      cursor += s.n;
+    }
+  }
+  ys_status st = ys_assign(plan, &dev[0], &dev[1]);
+  if (st != YS_OK) return st;
+  return ys_measure_multipoles(plan, out);
+}
+
+ys_status ys_plan_destroy(ys_plan* plan) {
+  if (!plan) return YS_OK;
+  Plan& p = plan->p;
+  if (p.stream) cudaStreamSynchronize(p.stream);
+  else cudaDeviceSynchronize();
+  if (p.measure_exec) cudaGraphExecDestroy(p.measure_exec);
+  if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
+  for (auto& ev : p.pending) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  for (cudaEvent_t ev : p.event_pool) cudaEventDestroy(ev);
+  ys::free_all(p);
+  delete plan;
+  return YS_OK;
+}
+
+ys_status ys_plan_set_profiling(ys_plan* plan, int enable) {
+  if (!plan) return YS_ERR_ARG;
+  plan->p.profiling = enable != 0;
+  return YS_OK;
+}
+
+ys_status ys_plan_get_stats(ys_plan* plan, ys_stats* out, int reset) {
+  if (!plan || !out) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  cudaError_t e = p.stream ? cudaStreamSynchronize(p.stream) : cudaDeviceSynchronize();
+  if (e) return ys::cuda_fail(e);
+  for (auto& ev : p.pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess) p.ms[ev.cls] += t;
+    p.event_pool.push_back(ev.a);
+    p.event_pool.push_back(ev.b);
+  }
+  p.pending.clear();
+  for (int c = 0; c < YS_NUM_KERNEL_CLASSES; ++c) {
+    out->launches[c] = p.launches[c];
+    out->ms[c] = p.ms[c];
+    if (reset) {
+      p.launches[c] = 0;
+      p.ms[c] = 0.0;
+    }
+  }
+  return YS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,362 @@
+// Step 1 of the estimator: F = w (n - alpha n_s) on the mesh (Eq. 1; Sec. 4 assigns
+// galaxies and randoms to a cubic mesh by CIC), plus the FP64 catalogue sums behind
+// alpha, the normalisation I and the shot noise S (Eqs. 1 and 3).
+//
+// GB300 design: particles arrive in random order, and a direct global atomic
+// deposit onto a 0.5-1 GB mesh would miss L2 on almost every update.  Instead a
+// counting sort groups particles by mesh tile (16 x 16 x 32 nodes, both meshes of an
+// interlaced pair held together), and one CTA per tile accumulates its nodes in
+// shared memory with shared-memory atomics, then writes the tile with coalesced
+// plain stores.  A particle whose stencil crosses tile borders is listed once per
+// tile it touches (at most 8), so tiles never write each other's nodes: no global
+// atomics on the mesh and no zero-fill pass.
+//
+//   k_count   : cell index per particle, FP64-accumulated sums, per-tile counts
+//   k_scan    : exclusive scan of the counts (one CTA)
+//   k_bin     : records (sub-cell offsets, signed weight, packed cell) per tile
+//   k_deposit : per-tile shared-memory deposit and store
+//
+// Sub-cell offsets are formed against a host-built FP64 table of node positions
+// split into float (hi, lo) pairs, so d = u - floor(u) keeps ~1e-7 accuracy even
+// where u = (x - box_min)/H itself is only good to ~1e-5 in float.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "ys_internal.h"
+
+namespace ys {
+namespace {
+
+constexpr int THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Cell index i and offset d in [0, 1) of coordinate x along one axis.  Returns
+// false (and a periodically wrapped in-range cell) when x lies outside the box.
+__device__ __forceinline__ bool locate(float x, int axis, const Geom& g, const float2* __restrict__ nodes,
+                                       int& i_out, float& d_out) {
+  const int n = g.n;
+  const float u0 = (x - g.bmin[axis]) * g.inv_h;
+  const bool finite = isfinite(u0);
+  const float uc = finite ? fminf(fmaxf(u0, -2.f), (float)n + 2.f) : 0.f;
+  int i = (int)floorf(uc);
+  i = max(-1, min(n, i));
+  const float2* nd = nodes + axis * (n + 3) + 1;  // nd[i] for i in [-1, n + 1]
+  float2 nv = nd[i];
+  float d = ((x - nv.x) - nv.y) * g.inv_h;
+  if (d < 0.f) {
+    i = max(i - 1, -1);
+    nv = nd[i];
+    d = ((x - nv.x) - nv.y) * g.inv_h;
+  } else if (d >= 1.f) {
+    i = min(i + 1, n);
+    nv = nd[i];
+    d = ((x - nv.x) - nv.y) * g.inv_h;
+  }
+  const bool ok = finite && i >= 0 && i < n && d >= 0.f && d < 1.f;
+  if (!ok) {
+    const float uw = finite ? u0 - floorf(u0 / (float)n) * (float)n : 0.f;
+    int iw = (int)floorf(uw);
+    iw = max(0, min(n - 1, iw));
+    i = iw;
+    d = fminf(fmaxf(uw - (float)iw, 0.f), 0.99999994f);
+  }
+  i_out = i;
+  d_out = d;
+  return ok;
+}
+
+// Stencil of one axis: up to KIND nodes and weights, for mesh 1 (nodes at i) and
+// mesh 2 (nodes at i + 1/2, i.e. coordinate u - 1/2).
+template <int KIND>
+__device__ __forceinline__ void stencil(int i, float d, bool second, int& first, float (&w)[3]) {
+  if (KIND == 1) {  // NGP
+    first = second ? i : i + (d >= 0.5f ? 1 : 0);
+    w[0] = 1.f;
+  } else if (KIND == 2) {  // CIC
+    int i2 = i;
+    float d2 = d;
+    if (second) {
+      if (d >= 0.5f) { d2 = d - 0.5f; } else { i2 = i - 1; d2 = d + 0.5f; }
+    }
+    first = i2;
+    w[0] = 1.f - d2;
+    w[1] = d2;
+  } else {  // TSC
+    int c;
+    float dd;
+    if (second) { c = i; dd = d - 0.5f; }
+    else if (d >= 0.5f) { c = i + 1; dd = d - 1.f; }
+    else { c = i; dd = d; }
+    first = c - 1;
+    const float a = 0.5f - dd, b = 0.5f + dd;
+    w[0] = 0.5f * a * a;
+    w[1] = 0.75f - dd * dd;
+    w[2] = 0.5f * b * b;
+  }
+}
+
+// Inclusive node range [lo, hi] covered by the stencils of the M meshes.
+template <int KIND, int M>
+__device__ __forceinline__ void node_range(int i, float d, int& lo, int& hi) {
+  float w[3];
+  int f1;
+  stencil<KIND>(i, d, false, f1, w);
+  lo = f1;
+  hi = f1 + KIND - 1;
+  if (M == 2) {
+    int f2;
+    stencil<KIND>(i, d, true, f2, w);
+    lo = min(lo, f2);
+    hi = max(hi, f2 + KIND - 1);
+  }
+}
+
+__device__ __forceinline__ int wrapn(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Tiles touched along one axis (1 or 2 of them).
+__device__ __forceinline__ int axis_tiles(int lo, int hi, int n, int tdim, int (&t)[2]) {
+  t[0] = wrapn(lo, n) / tdim;
+  t[1] = wrapn(hi, n) / tdim;
+  return t[0] == t[1] ? 1 : 2;
+}
+
+template <int KIND, int M, bool BIN>
+__global__ void __launch_bounds__(THREADS)
+k_particles(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
+            const float* __restrict__ pw, const float* __restrict__ pnbar, int64_t n, int is_ran,
+            Geom g, const float2* __restrict__ nodes, unsigned* __restrict__ tile_count,
+            unsigned* __restrict__ tile_cur, float4* __restrict__ rec, int* __restrict__ rec_cell,
+            double* __restrict__ sums, double alpha_cfg) {
+  // Compensated float sums per thread (Kahan), FP64 across threads.
+  float s_w = 0.f, c_w = 0.f, s_w2 = 0.f, c_w2 = 0.f, s_w2n = 0.f, c_w2n = 0.f;
+  unsigned bad = 0;
+  float wscale = 1.f;
+  if (BIN && is_ran) {
+    const double a = alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR];
+    wscale = (float)(-a);
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+    const float x = px[idx], y = py[idx], z = pz[idx];
+    const float w = pw ? pw[idx] : 1.f;
+    int ci[3];
+    float cd[3];
+    bool ok = locate(x, 0, g, nodes, ci[0], cd[0]);
+    ok &= locate(y, 1, g, nodes, ci[1], cd[1]);
+    ok &= locate(z, 2, g, nodes, ci[2], cd[2]);
+    int tt[3][2], nt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int lo, hi;
+      node_range<KIND, M>(ci[a], cd[a], lo, hi);
+      nt[a] = axis_tiles(lo, hi, g.n, g.tdim[a], tt[a]);
+    }
+    if (!BIN) {
+      bad += ok ? 0u : 1u;
+      {  // Kahan updates
+        float yv = w - c_w, t = s_w + yv;
+        c_w = (t - s_w) - yv; s_w = t;
+        yv = w * w - c_w2; t = s_w2 + yv;
+        c_w2 = (t - s_w2) - yv; s_w2 = t;
+        if (is_ran && pnbar) {
+          yv = w * w * pnbar[idx] - c_w2n; t = s_w2n + yv;
+          c_w2n = (t - s_w2n) - yv; s_w2n = t;
+        }
+      }
+    }
+    const float weff = w * wscale;
+    const int packed = (ci[0] << 20) | (ci[1] << 10) | ci[2];
+    for (int a = 0; a < nt[0]; ++a)
+      for (int b = 0; b < nt[1]; ++b)
+        for (int c = 0; c < nt[2]; ++c) {
+          const int tile = (tt[0][a] * g.tiles[1] + tt[1][b]) * g.tiles[2] + tt[2][c];
+          if (!BIN) {
+            atomicAdd(&tile_count[tile], 1u);
+          } else {
+            const unsigned slot = atomicAdd(&tile_cur[tile], 1u);
+            rec[slot] = make_float4(cd[0], cd[1], cd[2], weff);
+            rec_cell[slot] = packed;
+          }
+        }
+  }
+  if (!BIN) {
+    __shared__ double red[THREADS / 32][4];
+    double v0 = warp_sum((double)s_w - (double)c_w);
+    double v1 = warp_sum((double)s_w2 - (double)c_w2);
+    double v2 = warp_sum((double)s_w2n - (double)c_w2n);
+    double v3 = warp_sum((double)bad);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[wid][0] = v0; red[wid][1] = v1; red[wid][2] = v2; red[wid][3] = v3; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+      for (int k = 0; k < THREADS / 32; ++k) { t0 += red[k][0]; t1 += red[k][1]; t2 += red[k][2]; t3 += red[k][3]; }
+      if (is_ran) {
+        atomicAdd(&sums[SUM_WR], t0);
+        atomicAdd(&sums[SUM_WR2], t1);
+        atomicAdd(&sums[SUM_WR2N], t2);
+      } else {
+        atomicAdd(&sums[SUM_WG], t0);
+        atomicAdd(&sums[SUM_WG2], t1);
+      }
+      if (t3 != 0.0) atomicAdd(&sums[SUM_BAD], t3);
+    }
+  }
+}
+
+// Exclusive scan of the tile counts (single CTA of 1024 threads).
+__global__ void __launch_bounds__(1024)
+k_scan(const unsigned* __restrict__ count, int ntiles, unsigned* __restrict__ off, unsigned* __restrict__ cur) {
+  __shared__ unsigned part[1024];
+  const int t = threadIdx.x;
+  const int per = (ntiles + 1023) / 1024;
+  const int b = t * per, e = min(ntiles, b + per);
+  unsigned s = 0;
+  for (int i = b; i < e; ++i) s += count[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+    const unsigned v = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned run = t > 0 ? part[t - 1] : 0u;
+  for (int i = b; i < e; ++i) {
+    off[i] = run;
+    cur[i] = run;
+    run += count[i];
+  }
+  if (t == 1023) off[ntiles] = part[1023];
+}
+
+template <int KIND, int M>
+__global__ void __launch_bounds__(THREADS)
+k_deposit(Geom g, const unsigned* __restrict__ off, const float4* __restrict__ rec,
+          const int* __restrict__ rec_cell, float* __restrict__ mesh) {
+  extern __shared__ float s_tile[];
+  const int n = g.n;
+  const int tdx = g.tdim[0], tdy = g.tdim[1], tdz = g.tdim[2];
+  const int tvol = tdx * tdy * tdz;
+  const int tile = blockIdx.x;
+  const int tz = tile % g.tiles[2];
+  const int ty = (tile / g.tiles[2]) % g.tiles[1];
+  const int tx = tile / (g.tiles[2] * g.tiles[1]);
+  const int o[3] = {tx * tdx, ty * tdy, tz * tdz};
+  const int td[3] = {tdx, tdy, tdz};
+  for (int k = threadIdx.x; k < M * tvol; k += blockDim.x) s_tile[k] = 0.f;
+  __syncthreads();
+  const unsigned b = off[tile], e = off[tile + 1];
+  for (unsigned r = b + threadIdx.x; r < e; r += blockDim.x) {
+    const float4 q = rec[r];
+    const int packed = rec_cell[r];
+    const int ci[3] = {(packed >> 20) & 1023, (packed >> 10) & 1023, packed & 1023};
+    const float cd[3] = {q.x, q.y, q.z};
+#pragma unroll
+    for (int mj = 0; mj < M; ++mj) {
+      int loc[3][3];
+      float wt[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int first;
+        stencil<KIND>(ci[a], cd[a], mj == 1, first, wt[a]);
+#pragma unroll
+        for (int s = 0; s < KIND; ++s) {
+          const int l = wrapn(first + s - o[a], n);  // first + s in [-1, n + 1]; o[a] in [0, n)
+          loc[a][s] = (l >= 0 && l < td[a]) ? l : -1;
+        }
+      }
+      float* st = s_tile + mj * tvol;
+#pragma unroll
+      for (int a = 0; a < KIND; ++a) {
+        if (loc[0][a] < 0) continue;
+#pragma unroll
+        for (int bb = 0; bb < KIND; ++bb) {
+          if (loc[1][bb] < 0) continue;
+          const float wxy = q.w * wt[0][a] * wt[1][bb];
+          float* row = st + (loc[0][a] * tdy + loc[1][bb]) * tdz;
+#pragma unroll
+          for (int c = 0; c < KIND; ++c) {
+            if (loc[2][c] < 0) continue;
+            atomicAdd(row + loc[2][c], wxy * wt[2][c]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const size_t n3 = (size_t)n * n * n;
+  for (int k = threadIdx.x; k < M * tvol; k += blockDim.x) {
+    const int mj = k / tvol;
+    const int rr = k - mj * tvol;
+    const int lz = rr % tdz;
+    const int ly = (rr / tdz) % tdy;
+    const int lx = rr / (tdz * tdy);
+    mesh[mj * n3 + ((size_t)(o[0] + lx) * n + (o[1] + ly)) * n + (o[2] + lz)] = s_tile[k];
+  }
+}
+
+template <int KIND, int M>
+cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
+  cudaStream_t st = p.stream;
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(p.d_tile_count, 0, sizeof(unsigned) * p.ntiles, st)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(p.d_sums, 0, sizeof(double) * SUM_COUNT, st)) != cudaSuccess) return err;
+  auto blocks = [](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + THREADS - 1) / THREADS, 152 * 16)); };
+  const ys_catalog* cats[2] = {&gal, &ran};
+  for (int c = 0; c < 2; ++c) {
+    const ys_catalog& k = *cats[c];
+    if (k.n == 0) continue;
+    LaunchScope ls(p, 0);
+    k_particles<KIND, M, false><<<blocks(k.n), THREADS, 0, st>>>(
+        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr, nullptr,
+        p.d_sums, p.cfg.alpha);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  {
+    LaunchScope ls(p, 1);
+    k_scan<<<1, 1024, 0, st>>>(p.d_tile_count, p.ntiles, p.d_tile_off, p.d_tile_cur);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  for (int c = 0; c < 2; ++c) {
+    const ys_catalog& k = *cats[c];
+    if (k.n == 0) continue;
+    LaunchScope ls(p, 2);
+    k_particles<KIND, M, true><<<blocks(k.n), THREADS, 0, st>>>(
+        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, nullptr, p.d_tile_cur, p.d_rec, p.d_rec_cell,
+        p.d_sums, p.cfg.alpha);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const int tvol = p.geom.tdim[0] * p.geom.tdim[1] * p.geom.tdim[2];
+  const size_t smem = sizeof(float) * M * tvol;
+  if ((err = cudaFuncSetAttribute(k_deposit<KIND, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return err;
+  LaunchScope ls(p, 3);
+  k_deposit<KIND, M><<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_tile_off, p.d_rec, p.d_rec_cell, p.d_mesh);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
+  const int key = p.kind * 2 + (p.m - 1);
+  switch (key) {
+    case 2: return run_assign<1, 1>(p, gal, ran);
+    case 3: return run_assign<1, 2>(p, gal, ran);
+    case 4: return run_assign<2, 1>(p, gal, ran);
+    case 5: return run_assign<2, 2>(p, gal, ran);
+    case 6: return run_assign<3, 1>(p, gal, ran);
+    case 7: return run_assign<3, 2>(p, gal, ran);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ys

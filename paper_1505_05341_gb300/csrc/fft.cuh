@@ -1,0 +1,188 @@
+// Shared-memory complex FFTs for the mesh transforms (forward, e^{-2 pi i j k / N}).
+//
+// The paper (Sec. 3) only needs "any FFT algorithm"; this one is a Stockham
+// autosort decimation-in-time transform with the result in natural order.  N is
+// 2^a (radix-8 stages, then one radix-4 or radix-2) or 3 * 2^a (radix-4 stages, an
+// optional radix-2, then radix-3).  Each thread holds E = 8 (or 12) elements per line
+// and does E / R butterflies per stage; the data go through shared memory between
+// stages.  Twiddles come from a table tw[j] = exp(-2 pi i j / N) computed in FP64 on
+// the host and rounded to float.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ys {
+
+__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Elements per thread.
+__host__ __device__ constexpr int fft_elems(int n) { return is_pow2(n) ? 8 : 12; }
+
+// Number of stages and the radix of stage s (see header comment).
+__host__ __device__ constexpr int fft_nstages(int n) {
+  if (is_pow2(n)) {
+    int s = 0, m = n;
+    while (m >= 8) { m /= 8; ++s; }
+    return s + (m > 1 ? 1 : 0);
+  }
+  int s = 0, m = n / 3;
+  while (m % 4 == 0) { m /= 4; ++s; }
+  return s + (m == 2 ? 1 : 0) + 1;
+}
+
+__host__ __device__ constexpr int fft_radix(int n, int stage) {
+  if (is_pow2(n)) {
+    int m = n, s = 0;
+    while (m >= 8) { if (s == stage) return 8; m /= 8; ++s; }
+    return m;
+  }
+  int m = n / 3, s = 0;
+  while (m % 4 == 0) { if (s == stage) return 4; m /= 4; ++s; }
+  if (m == 2) { if (s == stage) return 2; ++s; }
+  return 3;
+}
+
+__host__ __device__ constexpr int fft_ns_before(int n, int stage) {
+  int ns = 1;
+  for (int s = 0; s < stage; ++s) ns *= fft_radix(n, s);
+  return ns;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// -i * a
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+template <int R> struct Dft;
+
+template <> struct Dft<2> {
+  __device__ static __forceinline__ void run(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <> struct Dft<3> {
+  __device__ static __forceinline__ void run(float2* v) {
+    // w = e^{-2 pi i / 3} = -1/2 - i sqrt(3)/2
+    const float s3 = 0.866025403784438647f;
+    const float2 a = v[0], b = v[1], c = v[2];
+    const float2 t1 = cadd(b, c);
+    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
+    const float2 d = csub(b, c);
+    const float2 t3 = make_float2(s3 * d.y, -s3 * d.x);  // -i sqrt3/2 (b - c)
+    v[0] = cadd(a, t1);
+    v[1] = cadd(t2, t3);
+    v[2] = csub(t2, t3);
+  }
+};
+
+template <> struct Dft<4> {
+  __device__ static __forceinline__ void run(float2* v) {
+    const float2 a = v[0], b = v[1], c = v[2], d = v[3];
+    const float2 s0 = cadd(a, c), s1 = csub(a, c);
+    const float2 s2 = cadd(b, d), s3 = cmul_mi(csub(b, d));
+    v[0] = cadd(s0, s2);
+    v[2] = csub(s0, s2);
+    v[1] = cadd(s1, s3);
+    v[3] = csub(s1, s3);
+  }
+};
+
+template <> struct Dft<8> {
+  __device__ static __forceinline__ void run(float2* v) {
+    // even / odd split into two DFT-4s, then w8^k = e^{-i pi k / 4}.
+    const float h = 0.707106781186547524f;
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4>::run(e);
+    Dft<4>::run(o);
+    const float2 o1 = make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));   // (1-i)/sqrt2
+    const float2 o2 = cmul_mi(o[2]);                                              // -i
+    const float2 o3 = make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));  // (-1-i)/sqrt2
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+// One Stockham stage over `nl` lines of length N stored in shared memory at
+// buf[line * ls + elem * es].  LF: consecutive threads take consecutive lines (for
+// layouts whose lines interleave); otherwise consecutive threads walk one line.
+template <int N, int S, bool LF>
+__device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, const float2* tw) {
+  constexpr int R = fft_radix(N, S);
+  constexpr int E = fft_elems(N);
+  constexpr int TPL = N / E;        // threads per line
+  constexpr int NB = E / R;         // butterflies per thread
+  constexpr int NS = fft_ns_before(N, S);
+  constexpr int STRIDE = N / R;
+  constexpr int TWS = N / (NS * R);
+  const int tid = threadIdx.x;
+  const int lpp = blockDim.x / TPL;  // lines per pass
+  const bool in_pass = tid < lpp * TPL;
+  const int lane_line = LF ? tid % lpp : tid / TPL;
+  const int tl = LF ? tid / lpp : tid % TPL;
+  for (int base_line = 0; base_line < nl; base_line += lpp) {
+    const int line = base_line + lane_line;
+    const bool ok = in_pass && line < nl;
+    float2 v[E];
+    if (ok) {
+      float2* lp = buf + (size_t)line * ls;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const int j = tl + q * TPL;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q * R + r] = lp[(j + r * STRIDE) * es];
+      }
+    }
+    __syncthreads();
+    if (ok) {
+      float2* lp = buf + (size_t)line * ls;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const int j = tl + q * TPL;
+        const int k = j % NS;
+        if (NS > 1) {
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tw[r * k * TWS]);
+        }
+        Dft<R>::run(&v[q * R]);
+        const int outb = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) lp[(outb + r * NS) * es] = v[q * R + r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Terminate the recursion at S == number of stages.
+template <int N, int S, bool LF, bool Done = (S >= fft_nstages(N))>
+struct FftRun {
+  __device__ static __forceinline__ void run(float2* buf, int es, int ls, int nl, const float2* tw) {
+    fft_stage<N, S, LF>(buf, es, ls, nl, tw);
+    FftRun<N, S + 1, LF>::run(buf, es, ls, nl, tw);
+  }
+};
+template <int N, int S, bool LF>
+struct FftRun<N, S, LF, true> {
+  __device__ static __forceinline__ void run(float2*, int, int, int, const float2*) {}
+};
+
+// In-place forward FFT of nl lines held in shared memory.  Every thread of the block
+// must call it (it contains __syncthreads).  blockDim.x must be >= N / E.
+template <int N, bool LF>
+__device__ __forceinline__ void fft_smem(float2* buf, int es, int ls, int nl, const float2* tw) {
+  FftRun<N, 0, LF>::run(buf, es, ls, nl, tw);
+}
+
+}  // namespace ys

@@ -1,0 +1,107 @@
+// Internal plan state and kernel entry points of the ystat library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/ystat.h"
+
+namespace ys {
+
+// Catalogue sums accumulated in FP64 (Eq. 1 and Eq. 3):
+enum SumSlot {
+  SUM_WG = 0,    // sum_gal w
+  SUM_WG2 = 1,   // sum_gal w^2
+  SUM_WR = 2,    // sum_ran w
+  SUM_WR2 = 3,   // sum_ran w^2
+  SUM_WR2N = 4,  // sum_ran w^2 nbar
+  SUM_BAD = 5,   // particles outside the box
+  SUM_HAS_NBAR = 6,
+  SUM_COUNT = 8
+};
+
+// Tile of the scatter: TX x TY x TZ mesh nodes per CTA (capped at N per axis).
+constexpr int TILE_X = 16, TILE_Y = 16, TILE_Z = 32;
+
+struct Geom {
+  int n;            // mesh side N
+  float inv_h;      // 1 / H
+  float bmin[3];    // box_min (float) for the first guess of the cell index
+  int tiles[3];     // tiles per axis
+  int tdim[3];      // tile extent per axis
+};
+
+struct Plan {
+  ys_config cfg;
+  cudaStream_t stream = nullptr;
+  int n = 0, m = 1, ell = 0, kind = 2;
+  int nb = 1, ng = 1;            // basis fields / k_x-power groups
+  double H = 0, kf = 0;
+  Geom geom{};
+  int ntiles = 0;
+  // pencils (k_y, k_z) kept for the x transform: k_y^2 + k_z^2 < n2_hi
+  int n2_hi = 0, nzc = 0, np = 0;
+  int batch = 1;                 // planes per y,z-transform batch
+  // device tables
+  float2* d_tw = nullptr;        // [n] exp(-2 pi i j / n)
+  float2* d_nodes = nullptr;     // [3][n + 3] node positions (hi, lo), index offset 1
+  float* d_rel = nullptr;        // [m][3][n] node - observer (float)
+  float* d_invw = nullptr;       // [n] per-axis 1 / sinc^p by FFT index (1 if !compensate)
+  float2* d_phase = nullptr;     // [n] per-axis exp(-i pi m / n) by FFT index
+  int* d_col_off = nullptr;      // [nzc + 1] first pencil of each k_z column
+  short2* d_pencil = nullptr;    // [np] (k_y signed, k_z)
+  short* d_lut = nullptr;        // [n2_hi] shell index of |m|^2, -1 = not used
+  double* d_shell = nullptr;     // [2][n_bins] mode count and sum |k| (host-built)
+  // buffers
+  float* d_mesh = nullptr;       // [m][n][n][n]
+  float2* d_z = nullptr;         // [nb][batch][nzc][n] y,z-stage scratch
+  float2* d_g = nullptr;         // [m][ng][n][np] grouped y,z transforms
+  double* d_acc = nullptr;       // [3][n_bins] shell sums
+  double* d_sums = nullptr;      // [SUM_COUNT]
+  double* d_result = nullptr;    // [5 n_bins + 3]
+  unsigned* d_tile_count = nullptr;  // [ntiles]
+  unsigned* d_tile_off = nullptr;    // [ntiles + 1]
+  unsigned* d_tile_cur = nullptr;    // [ntiles]
+  float4* d_rec = nullptr;       // [rec_cap] (dx, dy, dz, signed weight)
+  int* d_rec_cell = nullptr;     // [rec_cap] packed cell index
+  int64_t rec_cap = 0;
+  int64_t part_cap = 0;
+  // host staging for ys_estimate_host
+  float* d_stage = nullptr;
+  int64_t stage_cap = 0;
+  std::vector<double> h_result;
+  size_t device_bytes = 0;
+  bool assigned = false;
+  // CUDA graph of the measurement sequence (all pointers are plan-owned)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t measure_exec = nullptr;
+  int64_t measure_launches[YS_NUM_KERNEL_CLASSES] = {};
+  // statistics and optional event profiling
+  bool profiling = false;
+  bool capturing = false;
+  int64_t launches[YS_NUM_KERNEL_CLASSES] = {};
+  double ms[YS_NUM_KERNEL_CLASSES] = {};
+  struct EvPair { cudaEvent_t a, b; int cls; };
+  std::vector<EvPair> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// Brackets one kernel launch: counts it and, when profiling, records events.
+struct LaunchScope {
+  Plan& p;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(Plan& plan, int c);
+  ~LaunchScope();
+};
+
+// Kernel launchers (return cudaError_t of the launch).
+cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran);
+cudaError_t launch_measure(Plan& p);
+
+}  // namespace ys
+
+struct ys_plan_s {
+  ys::Plan p;
+};

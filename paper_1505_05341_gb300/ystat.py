@@ -1,0 +1,259 @@
+"""ctypes binding of libystat (include/ystat.h): argument marshalling only.
+
+Every step of the estimator runs in the library's CUDA kernels.  This module turns
+torch CUDA tensors (or numpy arrays, for the host entry point) into the C structs
+and back; it computes nothing itself.  If libystat.so has not been built, loading
+fails with an ImportError-style RuntimeError -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libystat.so")
+HEADER = os.path.join(HERE, "..", "include", "ystat.h")
+
+YS_OK, YS_ERR_ARG, YS_ERR_OOM, YS_ERR_CUDA, YS_ERR_TIMEOUT, YS_ERR_UNSUPPORTED, YS_ERR_STATE = range(7)
+ASSIGN = {"ngp": 1, "cic": 2, "tsc": 3}
+
+
+class YsConfig(ctypes.Structure):
+    _fields_ = [
+        ("n_mesh", ctypes.c_int32),
+        ("box_min", ctypes.c_double * 3),
+        ("box_len", ctypes.c_double),
+        ("observer", ctypes.c_double * 3),
+        ("assign", ctypes.c_int32),
+        ("interlace", ctypes.c_int32),
+        ("compensate", ctypes.c_int32),
+        ("ell_max", ctypes.c_int32),
+        ("k_min", ctypes.c_double),
+        ("dk", ctypes.c_double),
+        ("n_bins", ctypes.c_int32),
+        ("alpha", ctypes.c_double),
+        ("max_particles", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class YsCatalog(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+        ("z", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("nbar", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+    ]
+
+
+class YsResult(ctypes.Structure):
+    _fields_ = [
+        ("k_mean", ctypes.c_void_p),
+        ("n_modes", ctypes.c_void_p),
+        ("p0", ctypes.c_void_p),
+        ("p2", ctypes.c_void_p),
+        ("p4", ctypes.c_void_p),
+        ("alpha", ctypes.c_double),
+        ("norm_I", ctypes.c_double),
+        ("shot_noise", ctypes.c_double),
+    ]
+
+
+NUM_KERNEL_CLASSES = 8
+KERNEL_CLASSES = ["particle_count", "tile_scan", "particle_bin", "tile_deposit", "yz_rows", "yz_cols",
+                  "x_combine", "finalize"]
+
+
+class YsStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * NUM_KERNEL_CLASSES), ("ms", ctypes.c_double * NUM_KERNEL_CLASSES)]
+
+
+class YstatError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib().ys_status_string(status).decode()
+        if status == YS_ERR_CUDA:
+            msg += ": " + _lib().ys_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libystat.so is not built ({LIB_PATH}); run "
+                               "python -m paper_1505_05341_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        lib.ys_plan_create.argtypes = [ctypes.POINTER(YsConfig), ctypes.POINTER(P)]
+        lib.ys_plan_device_bytes.argtypes = [P]
+        lib.ys_plan_device_bytes.restype = ctypes.c_size_t
+        lib.ys_assign.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog)]
+        lib.ys_measure_multipoles_async.argtypes = [P, P]
+        lib.ys_measure_multipoles.argtypes = [P, ctypes.POINTER(YsResult)]
+        lib.ys_estimate_host.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog),
+                                         ctypes.POINTER(YsResult)]
+        lib.ys_plan_destroy.argtypes = [P]
+        lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
+        lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
+        lib.ys_status_string.argtypes = [ctypes.c_int]
+        lib.ys_status_string.restype = ctypes.c_char_p
+        lib.ys_last_cuda_error.restype = ctypes.c_char_p
+        for name in ("ys_plan_create", "ys_assign", "ys_measure_multipoles_async",
+                     "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
+                     "ys_plan_set_profiling", "ys_plan_get_stats"):
+            getattr(lib, name).restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def load_library():
+    """Load libystat.so (raises if it is missing)."""
+    return _lib()
+
+
+def header_functions():
+    """Names of the functions include/ystat.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ys_[a-z_]+)\s*\(", txt)))
+
+
+@dataclasses.dataclass
+class Result:
+    k: np.ndarray
+    n_modes: np.ndarray
+    p0: np.ndarray
+    p2: np.ndarray
+    p4: np.ndarray
+    alpha: float
+    norm_I: float
+    shot_noise: float
+    status: int = YS_OK
+
+
+def _check(status, where, allow=()):
+    if status != YS_OK and status not in allow:
+        raise YstatError(status, where)
+    return status
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Plan:
+    """One estimator configuration on the current CUDA device (ys_plan)."""
+
+    def __init__(self, n_mesh, box_min, box_len, observer=(0.0, 0.0, 0.0), assign="cic",
+                 interlace=False, compensate=True, ell_max=4, k_min=0.0, dk=0.01, n_bins=None,
+                 k_max=None, alpha=-1.0, max_particles=0, stream=None):
+        lib = _lib()
+        if n_bins is None:
+            kmax = k_max if k_max is not None else np.pi * n_mesh / box_len
+            n_bins = int(np.ceil((kmax - k_min) / dk - 1e-9))
+        cfg = YsConfig()
+        cfg.n_mesh = n_mesh
+        cfg.box_min = (ctypes.c_double * 3)(*box_min)
+        cfg.box_len = box_len
+        cfg.observer = (ctypes.c_double * 3)(*observer)
+        cfg.assign = ASSIGN[assign] if isinstance(assign, str) else int(assign)
+        cfg.interlace = int(bool(interlace))
+        cfg.compensate = int(bool(compensate))
+        cfg.ell_max = ell_max
+        cfg.k_min = k_min
+        cfg.dk = dk
+        cfg.n_bins = n_bins
+        cfg.alpha = alpha
+        cfg.max_particles = int(max_particles)
+        cfg.stream = stream
+        self.cfg = cfg
+        self.n_bins = n_bins
+        h = ctypes.c_void_p()
+        _check(lib.ys_plan_create(ctypes.byref(cfg), ctypes.byref(h)), "ys_plan_create")
+        self._h = h
+        self._keep = None
+
+    @property
+    def device_bytes(self):
+        return _lib().ys_plan_device_bytes(self._h)
+
+    @staticmethod
+    def _cat(x, y, z, w=None, nbar=None):
+        c = YsCatalog()
+        c.x, c.y, c.z, c.w, c.nbar = _ptr(x), _ptr(y), _ptr(z), _ptr(w), _ptr(nbar)
+        c.n = int(x.shape[0])
+        return c
+
+    def assign(self, gal, ran):
+        """gal, ran: dicts or tuples of device float32 tensors (x, y, z, w, nbar)."""
+        g = self._cat(*gal)
+        r = self._cat(*ran)
+        self._keep = (gal, ran)
+        _check(_lib().ys_assign(self._h, ctypes.byref(g), ctypes.byref(r)), "ys_assign")
+
+    def measure_async(self, d_out=None):
+        _check(_lib().ys_measure_multipoles_async(self._h, _ptr(d_out)), "ys_measure_multipoles_async")
+
+    def _result_struct(self):
+        nb = self.n_bins
+        arrs = [np.empty(nb, dtype=np.float64) for _ in range(5)]
+        res = YsResult()
+        res.k_mean, res.n_modes, res.p0, res.p2, res.p4 = [a.ctypes.data for a in arrs]
+        return res, arrs
+
+    def measure(self, allow_outside=False):
+        res, arrs = self._result_struct()
+        st = _check(_lib().ys_measure_multipoles(self._h, ctypes.byref(res)), "ys_measure_multipoles",
+                    allow=(YS_ERR_ARG,) if allow_outside else ())
+        return Result(*arrs, res.alpha, res.norm_I, res.shot_noise, st)
+
+    def estimate_host(self, gal, ran):
+        """End to end from host numpy float32 arrays (x, y, z, w, nbar)."""
+        gal = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in gal]
+        ran = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in ran]
+        g = self._cat(*gal)
+        r = self._cat(*ran)
+        res, arrs = self._result_struct()
+        st = _check(_lib().ys_estimate_host(self._h, ctypes.byref(g), ctypes.byref(r), ctypes.byref(res)),
+                    "ys_estimate_host")
+        return Result(*arrs, res.alpha, res.norm_I, res.shot_noise, st)
+
+    def set_profiling(self, enable: bool):
+        _check(_lib().ys_plan_set_profiling(self._h, int(bool(enable))), "ys_plan_set_profiling")
+
+    def stats(self, reset=False):
+        """{kernel class: (launches, summed device ms)} since the last reset."""
+        st = YsStats()
+        _check(_lib().ys_plan_get_stats(self._h, ctypes.byref(st), int(bool(reset))), "ys_plan_get_stats")
+        return {name: (int(st.launches[i]), float(st.ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().ys_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
