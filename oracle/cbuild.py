@@ -12,7 +12,7 @@ def build(force=False):
     srcs = [os.path.join(HERE, "c", f) for f in sorted(os.listdir(os.path.join(HERE, "c"))) if f.endswith(".c")]
     if not force and os.path.exists(LIB) and all(os.path.getmtime(s) <= os.path.getmtime(LIB) for s in srcs):
         return LIB
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", LIB + ".tmp", *srcs, "-lm"], check=True)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", LIB + ".tmp", *srcs, "-lm"], check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -50,16 +50,20 @@ __device__ __forceinline__ bool locate(float x, int axis, const Geom& g, const f
   const float2* nd = nodes + axis * (n + 3) + 1;  // nd[i] for i in [-1, n + 1]
   float2 nv = nd[i];
   float d = ((x - nv.x) - nv.y) * g.inv_h;
+  // One-cell correction of the float guess; a particle within rounding of a node can
+  // land on d = 1.0f (or a hair below 0) after it, so d is clamped into [0, 1):
+  // the stencils are continuous across the node, so either side gives the same mesh.
   if (d < 0.f) {
     i = max(i - 1, -1);
     nv = nd[i];
-    d = ((x - nv.x) - nv.y) * g.inv_h;
+    d = fminf(((x - nv.x) - nv.y) * g.inv_h, 0.99999994f);
   } else if (d >= 1.f) {
     i = min(i + 1, n);
     nv = nd[i];
-    d = ((x - nv.x) - nv.y) * g.inv_h;
+    d = fmaxf(((x - nv.x) - nv.y) * g.inv_h, 0.f);
   }
-  const bool ok = finite && i >= 0 && i < n && d >= 0.f && d < 1.f;
+  d = fminf(fmaxf(d, 0.f), 0.99999994f);
+  const bool ok = finite && i >= 0 && i < n;
   if (!ok) {
     const float uw = finite ? u0 - floorf(u0 / (float)n) * (float)n : 0.f;
     int iw = (int)floorf(uw);
