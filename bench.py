@@ -41,6 +41,11 @@ WORKLOAD = "shell512_tsc_il"
 N_MESH = 512
 K_MAX = 0.4
 DK = 0.01
+# Other workloads, for profiling captures that must stay small on the device.
+WORKLOADS = {
+    "shell512_tsc_il": dict(n_mesh=512, k_max=0.4),
+    "cone256_tsc_il": dict(n_mesh=256, k_max=None),   # up to Nyquist
+}
 
 
 def _cores():
@@ -119,9 +124,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_workload(rank):
+def make_workload(rank, name=WORKLOAD):
     import synth
-    return synth.poisson_shell(10_000_000, 50_000_000, seed_gal=4 + 100 * rank, seed_ran=5 + 100 * rank)
+    if name == "shell512_tsc_il":
+        return synth.poisson_shell(10_000_000, 50_000_000, seed_gal=4 + 100 * rank, seed_ran=5 + 100 * rank)
+    if name == "cone256_tsc_il":
+        return synth.zeldovich_cone(seed_field=2 + 100 * rank, seed_ran=3 + 100 * rank)
+    raise KeyError(name)
 
 
 def alg_bytes(n_gal, n_ran, n, m, groups, n_pencils):
@@ -222,7 +231,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    gal, ran, geo = make_workload(rank)
+    global N_MESH, K_MAX
+    wl = WORKLOADS[args.workload]
+    gal, ran, geo = make_workload(rank, args.workload)
+    N_MESH = wl["n_mesh"]
+    K_MAX = wl["k_max"] if wl["k_max"] is not None else math.pi * N_MESH / geo.box_len
     dev = lambda c: tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (c.x, c.y, c.z, c.w, c.nbar))
     dgal, dran = dev(gal), dev(ran)
     stream = torch.cuda.current_stream()
@@ -302,7 +315,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_mesh": N_MESH, "assign": "tsc", "interlace": True, "ell_max": 4,
+        "config": {"workload": args.workload, "n_mesh": N_MESH, "assign": "tsc", "interlace": True, "ell_max": 4,
                    "n_gal": gal.n, "n_ran": ran.n, "k_max": K_MAX, "dk": DK, "fields": "1+6+15",
                    "l2": "inputs larger than L2 (0.96 GB catalogue, 1 GB meshes, 11 GB spectra)",
                    "parallelism": f"replicas{world}"},
@@ -358,6 +371,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -159,6 +159,37 @@ ys_status ys_plan_set_profiling(ys_plan* plan, int enable);
  * last reset; reset != 0 clears them afterwards. */
 ys_status ys_plan_get_stats(ys_plan* plan, ys_stats* out, int reset);
 
+/* ys_assign without any device allocation.  (The paper has no counterpart; this is
+ * a deployment variant of the assignment step.)
+ *
+ * ys_assign keeps its sorting scratch -- per-tile counters and one record per
+ * (particle, mesh tile it touches) -- in plan-owned buffers sized to the largest
+ * catalogue seen, and grows them with cudaMalloc when a larger one arrives.  Callers
+ * that must not allocate device memory after set-up (a fixed memory pool, an
+ * embedding framework that owns every allocation, code that must not synchronise
+ * the device the way cudaMalloc/cudaFree can) use this entry point instead: it takes
+ * that scratch from one static device array of YS_NOALLOC_SCRATCH_BYTES (64 MiB) that
+ * every GPU loading the library holds until the process exits, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The plan must already exist
+ * (ys_plan_create allocates the mesh it writes; max_particles may be 0).
+ *
+ * Inputs: gal, ran with DEVICE pointers, as for ys_assign.  Output: the plan's mesh(es)
+ * and catalogue sums, consumed by the next ys_measure_multipoles*.  Asynchronous on
+ * the plan's stream.
+ * Limits: the records need (gal->n + ran->n) * T * 20 bytes, T = 2^(axes with more
+ * than one 16/16/32-node tile) <= 8, plus 12 bytes per tile; a catalogue that does
+ * not fit returns YS_ERR_UNSUPPORTED before any work is queued (ys_last_cuda_error()
+ * then gives the sizes).  For a 256^3 mesh (T = 8) this is about 400 000 particles.
+ * Set-up: the first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call before
+ * any stream capture.
+ * Sharing: every call, on every plan, uses the same array and leaves its contents
+ * behind; each call zeroes the counters it needs itself.  Calls whose work overlaps
+ * on the GPU (different streams, different host threads) race on the array and must
+ * be serialised by the caller. */
+#define YS_NOALLOC_SCRATCH_BYTES (64u << 20)
+ys_status ys_assign_noalloc(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran);
+
 /* Free everything the plan owns.  NULL is accepted. */
 ys_status ys_plan_destroy(ys_plan* plan);
 

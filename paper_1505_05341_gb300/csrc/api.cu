@@ -377,6 +377,14 @@ ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran)
   return YS_OK;
 }
 
+ys_status ys_assign_noalloc(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran) {
+  if (!plan || !ys::catalog_ok(gal) || !ys::catalog_ok(ran)) return YS_ERR_ARG;
+  std::string why;
+  const ys_status st = ys::assign_noalloc(plan->p, *gal, *ran, why);
+  if (st != YS_OK) ys::g_last_cuda_error = why;
+  return st;
+}
+
 ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out) {
   if (!plan) return YS_ERR_ARG;
   Plan& p = plan->p;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "../../include/ystat.h"
@@ -99,6 +100,7 @@ struct LaunchScope {
 // Kernel launchers (return cudaError_t of the launch).
 cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran);
 cudaError_t launch_measure(Plan& p);
+ys_status assign_noalloc(Plan& p, const ys_catalog& gal, const ys_catalog& ran, std::string& why);
 
 }  // namespace ys
 

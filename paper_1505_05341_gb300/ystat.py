@@ -103,6 +103,7 @@ def _lib():
         lib.ys_estimate_host.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog),
                                          ctypes.POINTER(YsResult)]
         lib.ys_plan_destroy.argtypes = [P]
+        lib.ys_assign_noalloc.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog)]
         lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
         lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
         lib.ys_status_string.argtypes = [ctypes.c_int]
@@ -110,7 +111,7 @@ def _lib():
         lib.ys_last_cuda_error.restype = ctypes.c_char_p
         for name in ("ys_plan_create", "ys_assign", "ys_measure_multipoles_async",
                      "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
-                     "ys_plan_set_profiling", "ys_plan_get_stats"):
+                     "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
     return _LIB
