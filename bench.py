@@ -148,10 +148,8 @@ def kernel_bytes(cls, n_gal, n_ran, n, m, groups, n_pencils, launches_per_step, 
         return 16 * (n_gal + n_ran) / 2
     if cls == "tile_deposit":
         return m * 4 * n ** 3
-    if cls == "yz_rows":
-        return m * 4 * n ** 3 / launches_per_step
-    if cls == "yz_cols":
-        return m * groups * 8 * n * n_pencils / launches_per_step
+    if cls == "yz_stage":
+        return (m * 4 * n ** 3 + m * groups * 8 * n * n_pencils) / launches_per_step
     if cls == "x_combine":
         return m * groups * 8 * n * n_pencils
     return 0.0
@@ -242,7 +240,7 @@ def run_ours(args):
     n_bins = int(math.ceil(K_MAX / DK - 1e-9))
     plan = ys.Plan(N_MESH, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, ell_max=4,
                    dk=DK, n_bins=n_bins, max_particles=gal.n + ran.n, stream=stream.cuda_stream)
-    out = torch.empty(5 * n_bins + 4, dtype=torch.float64, device="cuda")
+    out = torch.empty(5 * n_bins + 5, dtype=torch.float64, device="cuda")
 
     def step():
         plan.assign(dgal, dran)
@@ -327,7 +325,7 @@ def run_ours(args):
         "kernels": {k: {"launches_per_step": v[0], "avg_ms": v[1]} for k, v in per_cls.items()},
         "clocks": clk.summary(),
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 20 * (gal.n + ran.n),
-                "d2h_bytes_per_step": 8 * (5 * n_bins + 4)},
+                "d2h_bytes_per_step": 8 * (5 * n_bins + 5)},
         "gpu_launches": gpu_launches,
         "p0_first_bins": [float(v) for v in res.p0[:3]],
     }

@@ -126,7 +126,8 @@ ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran)
 ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out);
 
 /* As ys_measure_multipoles_async, then waits for the stream and copies the result
- * into the caller's host arrays.  Returns YS_ERR_ARG if ys_assign saw particles
+ * into the caller's host arrays.  Returns YS_ERR_TIMEOUT if a bounded device-side
+ * wait ran out (results invalid), else YS_ERR_ARG if ys_assign saw particles
  * outside the box (results are still written). */
 ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out);
 
@@ -141,8 +142,8 @@ ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalo
  * the plan's stream and ys_measure_multipoles* launches directly instead of
  * replaying its captured CUDA graph.  Kernel classes, in order:
  *   0 particle count + catalogue sums, 1 tile scan, 2 particle binning,
- *   3 tile deposit, 4 y,z-stage rows (fields + FFT along z), 5 y,z-stage columns
- *   (FFT along y + k_x-power grouping), 6 x-stage (FFT along x + combine + shells),
+ *   3 tile deposit, 4 y,z stage (LOS fields, FFTs along z and y, k_x-power grouping;
+ *   one persistent launch), 5 (unused), 6 x-stage (FFT along x + combine + shells),
  *   7 finalize.
  * launches[c] counts kernel launches of class c, ms[c] their summed device time
  * (valid only for launches made while profiling was on). */

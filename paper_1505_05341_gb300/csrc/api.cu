@@ -14,6 +14,8 @@
 namespace ys {
 
 template <int N> cudaError_t run_measure_n(Plan& p);
+template <int N> int yz_grid_n(int ell, cudaError_t* err);
+template <int N> int x_pencils_n();
 
 namespace {
 
@@ -51,15 +53,15 @@ void dfree(T*& ptr) {
 void free_all(Plan& p) {
   dfree(p.d_tw); dfree(p.d_nodes); dfree(p.d_rel); dfree(p.d_invw); dfree(p.d_phase);
   dfree(p.d_col_off); dfree(p.d_pencil); dfree(p.d_lut); dfree(p.d_shell);
-  dfree(p.d_mesh); dfree(p.d_z); dfree(p.d_g); dfree(p.d_acc); dfree(p.d_sums); dfree(p.d_result);
+  dfree(p.d_mesh); dfree(p.d_z); dfree(p.d_sync); dfree(p.d_g); dfree(p.d_acc); dfree(p.d_sums); dfree(p.d_result);
   dfree(p.d_tile_count); dfree(p.d_tile_off); dfree(p.d_tile_cur); dfree(p.d_rec); dfree(p.d_rec_cell);
   dfree(p.d_stage);
   p.device_bytes = 0;
 }
 
 __global__ void k_finalize(const double* __restrict__ acc, const double* __restrict__ shell,
-                           const double* __restrict__ sums, double alpha_cfg, int nbins, int ell,
-                           double* __restrict__ res) {
+                           const double* __restrict__ sums, const int* __restrict__ flags, double alpha_cfg,
+                           int nbins, int ell, double* __restrict__ res) {
   const double alpha = alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR];
   const double I = alpha * sums[SUM_WR2N];
   const double S = sums[SUM_WG2] + alpha * alpha * sums[SUM_WR2];
@@ -86,7 +88,53 @@ __global__ void k_finalize(const double* __restrict__ acc, const double* __restr
     res[5 * nbins + 1] = I;
     res[5 * nbins + 2] = S / I;
     res[5 * nbins + 3] = sums[SUM_BAD];
+    res[5 * nbins + 4] = (double)flags[0];
   }
+}
+
+int x_pencils_for(int n) {
+  switch (n) {
+    case 16: return x_pencils_n<16>();
+    case 32: return x_pencils_n<32>();
+    case 64: return x_pencils_n<64>();
+    case 96: return x_pencils_n<96>();
+    case 128: return x_pencils_n<128>();
+    case 192: return x_pencils_n<192>();
+    case 256: return x_pencils_n<256>();
+    case 384: return x_pencils_n<384>();
+    case 512: return x_pencils_n<512>();
+    case 768: return x_pencils_n<768>();
+    default: return x_pencils_n<1024>();
+  }
+}
+
+// 2D tensor map over the grouped transforms d_g: rows = (mesh, group, x), columns =
+// 2 np_pad floats (np_pad float2 pencils); box = (2 P floats, min(N, 256) rows).
+ys_status make_gmap(Plan& p) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess) {
+    g_last_cuda_error = "cuTensorMapEncodeTiled not available";
+    return YS_ERR_CUDA;
+  }
+  auto encode = reinterpret_cast<CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                              CUtensorMapFloatOOBfill)>(fn);
+  const int P = x_pencils_for(p.n);
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * p.np_pad, (cuuint64_t)p.m * p.ng * p.n};
+  const cuuint64_t strides[1] = {(cuuint64_t)2 * p.np_pad * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * P), (cuuint32_t)std::min(p.n, 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&p.gmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.d_g, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    g_last_cuda_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return YS_ERR_CUDA;
+  }
+  return YS_OK;
 }
 
 // FP64 host tables (shells, pencils, windows, phases, twiddles, node positions).
@@ -125,6 +173,10 @@ ys_status build_tables(Plan& p) {
   }
   p.nzc = nzc;
   p.np = (int)pen.size();
+  // pad to whole x-stage pencil blocks with pencils that match no shell (k_z = -1)
+  const int xp = x_pencils_for(n);
+  p.np_pad = std::max(xp, (p.np + xp - 1) / xp * xp);
+  while ((int)pen.size() < p.np_pad) pen.push_back(make_short2(0, -1));
   // mode count and sum |k| per shell (half grid, weight 2 for 0 < k_z < n/2)
   std::vector<double> shell(2 * c.n_bins, 0.0);
   for (int kz = 0; kz < nzc; ++kz) {
@@ -244,9 +296,35 @@ LaunchScope::~LaunchScope() {
 
 cudaError_t launch_finalize(Plan& p) {
   LaunchScope ls(p, 7);
-  k_finalize<<<1, 256, 0, p.stream>>>(p.d_acc, p.d_shell, p.d_sums, p.cfg.alpha, p.cfg.n_bins, p.ell,
-                                      p.d_result);
+  k_finalize<<<1, 256, 0, p.stream>>>(p.d_acc, p.d_shell, p.d_sums, p.d_sync + 2 * p.m * p.n + 1, p.cfg.alpha,
+                                      p.cfg.n_bins, p.ell, p.d_result);
   return cudaGetLastError();
+}
+
+// Row items per plane of the y,z kernel (N / rows per item; mirrors YZ<N, ELL>::R).
+int yz_row_items(int n) {
+  const int E = (n & (n - 1)) == 0 ? (n >= 512 ? 16 : 8) : (n >= 768 ? 24 : 12);
+  const int lpp = 256 / (n / E);
+  const int base = n >= 512 ? 8 : 16;
+  const int r = lpp > base ? std::min(lpp, n) : base;
+  return n / r;
+}
+
+int yz_grid_for(Plan& p, cudaError_t* err) {
+  switch (p.n) {
+    case 16: return yz_grid_n<16>(p.ell, err);
+    case 32: return yz_grid_n<32>(p.ell, err);
+    case 64: return yz_grid_n<64>(p.ell, err);
+    case 96: return yz_grid_n<96>(p.ell, err);
+    case 128: return yz_grid_n<128>(p.ell, err);
+    case 192: return yz_grid_n<192>(p.ell, err);
+    case 256: return yz_grid_n<256>(p.ell, err);
+    case 384: return yz_grid_n<384>(p.ell, err);
+    case 512: return yz_grid_n<512>(p.ell, err);
+    case 768: return yz_grid_n<768>(p.ell, err);
+    case 1024: return yz_grid_n<1024>(p.ell, err);
+    default: *err = cudaErrorInvalidValue; return 0;
+  }
 }
 
 cudaError_t launch_measure(Plan& p) {
@@ -337,15 +415,32 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
     return st;
   }
   const size_t n3 = (size_t)n * n * n;
-  const size_t plane_scratch = (size_t)p.nb * std::max(1, p.nzc) * n * sizeof(float2);
-  p.batch = (int)std::max<size_t>(1, std::min<size_t>(n, (48u << 20) / plane_scratch));
-  if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, plane_scratch / sizeof(float2) * p.batch)) ||
-      (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np))) ||
+  // y,z-stage ring: the column items of a plane trail its row items by D planes, and a
+  // slot is rewritten S = D + 2 planes later; D covers one grid's worth of items.
+  p.yz_grid = ys::yz_grid_for(p, &e);
+  if (e) {
+    st = ys::cuda_fail(e);
+    ys::free_all(p);
+    delete h;
+    return st;
+  }
+  const int items_per_plane = ys::yz_row_items(p.n) + std::max(1, p.nzc);
+  p.ring_lead = (p.yz_grid + items_per_plane - 1) / items_per_plane + 1;
+  p.ring_slots = std::min(p.m * n, p.ring_lead + 2);
+  const size_t slot = (size_t)p.nb * std::max(1, p.nzc) * n;
+  if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, slot * p.ring_slots)) ||
+      (e = ys::dalloc(p, p.d_sync, (size_t)2 * p.m * n + 2)) ||
+      (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np_pad))) ||
       (e = ys::dalloc(p, p.d_acc, (size_t)3 * c.n_bins)) || (e = ys::dalloc(p, p.d_sums, (size_t)ys::SUM_COUNT)) ||
-      (e = ys::dalloc(p, p.d_result, (size_t)5 * c.n_bins + 4)) ||
+      (e = ys::dalloc(p, p.d_result, (size_t)5 * c.n_bins + 5)) ||
       (e = ys::dalloc(p, p.d_tile_count, (size_t)p.ntiles)) || (e = ys::dalloc(p, p.d_tile_off, (size_t)p.ntiles + 1)) ||
       (e = ys::dalloc(p, p.d_tile_cur, (size_t)p.ntiles))) {
     st = ys::cuda_fail(e);
+    ys::free_all(p);
+    delete h;
+    return st;
+  }
+  if (p.np > 0 && (st = ys::make_gmap(p)) != YS_OK) {
     ys::free_all(p);
     delete h;
     return st;
@@ -355,7 +450,7 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
     delete h;
     return st;
   }
-  p.h_result.assign((size_t)5 * c.n_bins + 4, 0.0);
+  p.h_result.assign((size_t)5 * c.n_bins + 5, 0.0);
   if (cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     p.cap_stream = nullptr;
@@ -425,7 +520,7 @@ ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out) {
     if (e) return ys::cuda_fail(e);
   }
   if (d_out) {
-    e = cudaMemcpyAsync(d_out, p.d_result, sizeof(double) * (5 * p.cfg.n_bins + 4), cudaMemcpyDeviceToDevice,
+    e = cudaMemcpyAsync(d_out, p.d_result, sizeof(double) * (5 * p.cfg.n_bins + 5), cudaMemcpyDeviceToDevice,
                         p.stream);
     if (e) return ys::cuda_fail(e);
   }
@@ -438,7 +533,7 @@ ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out) {
   ys_status st = ys_measure_multipoles_async(plan, nullptr);
   if (st != YS_OK) return st;
   const int nb = p.cfg.n_bins;
-  cudaError_t e = cudaMemcpyAsync(p.h_result.data(), p.d_result, sizeof(double) * (5 * nb + 4),
+  cudaError_t e = cudaMemcpyAsync(p.h_result.data(), p.d_result, sizeof(double) * (5 * nb + 5),
                                   cudaMemcpyDeviceToHost, p.stream);
   if (e) return ys::cuda_fail(e);
   if ((e = cudaStreamSynchronize(p.stream))) return ys::cuda_fail(e);
@@ -449,6 +544,7 @@ ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out) {
   out->alpha = r[5 * nb + 0];
   out->norm_I = r[5 * nb + 1];
   out->shot_noise = r[5 * nb + 2];
+  if (r[5 * nb + 4] != 0) return YS_ERR_TIMEOUT;
   return r[5 * nb + 3] > 0 ? YS_ERR_ARG : YS_OK;
 }
 

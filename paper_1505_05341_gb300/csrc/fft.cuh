@@ -14,8 +14,15 @@ namespace ys {
 
 __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// Elements per thread.
-__host__ __device__ constexpr int fft_elems(int n) { return is_pow2(n) ? 8 : 12; }
+// Elements per thread: chosen so that one line is handled by at most one warp
+// (N / E <= 32) up to N = 512 (and 768), which lets the stages synchronise with
+// __syncwarp instead of a block-wide barrier.
+__host__ __device__ constexpr int fft_elems(int n) {
+  return is_pow2(n) ? (n >= 512 ? 16 : 8) : (n >= 768 ? 24 : 12);
+}
+
+// Elements per thread for layouts whose lines interleave (x-stage): 8 or 12.
+__host__ __device__ constexpr int fft_elems_lf(int n) { return is_pow2(n) ? 8 : 12; }
 
 // Number of stages and the radix of stage s (see header comment).
 __host__ __device__ constexpr int fft_nstages(int n) {
@@ -114,18 +121,30 @@ template <> struct Dft<8> {
   }
 };
 
+// Element offset inside a line: with PAD, one complex of padding follows every 8
+// elements, which spreads the strided Stockham stores over the shared-memory banks.
+template <bool PAD>
+__host__ __device__ constexpr int fft_pos(int i) { return PAD ? i + (i >> 3) : i; }
+
+// Line length in complex elements for a padded / unpadded layout (odd, so that
+// consecutive lines start in different banks).
+template <int N, bool PAD>
+__host__ __device__ constexpr int fft_line_len() { return PAD ? N + N / 8 + 1 : N + 1; }
+
 // One Stockham stage over `nl` lines of length N stored in shared memory at
 // buf[line * ls + elem * es].  LF: consecutive threads take consecutive lines (for
 // layouts whose lines interleave); otherwise consecutive threads walk one line.
-template <int N, int S, bool LF>
+template <int N, int S, bool LF, bool PAD>
 __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, const float2* tw) {
   constexpr int R = fft_radix(N, S);
-  constexpr int E = fft_elems(N);
+  constexpr int E = LF ? fft_elems_lf(N) : fft_elems(N);
   constexpr int TPL = N / E;        // threads per line
   constexpr int NB = E / R;         // butterflies per thread
   constexpr int NS = fft_ns_before(N, S);
   constexpr int STRIDE = N / R;
   constexpr int TWS = N / (NS * R);
+  // A line lives inside one warp when it is walked by consecutive threads and TPL <= 32.
+  constexpr bool WARP_LOCAL = !LF && TPL <= 32;
   const int tid = threadIdx.x;
   const int lpp = blockDim.x / TPL;  // lines per pass
   const bool in_pass = tid < lpp * TPL;
@@ -141,10 +160,10 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, c
       for (int q = 0; q < NB; ++q) {
         const int j = tl + q * TPL;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q * R + r] = lp[(j + r * STRIDE) * es];
+        for (int r = 0; r < R; ++r) v[q * R + r] = lp[fft_pos<PAD>(j + r * STRIDE) * es];
       }
     }
-    __syncthreads();
+    if (WARP_LOCAL) __syncwarp(); else __syncthreads();
     if (ok) {
       float2* lp = buf + (size_t)line * ls;
 #pragma unroll
@@ -158,31 +177,101 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, c
         Dft<R>::run(&v[q * R]);
         const int outb = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) lp[(outb + r * NS) * es] = v[q * R + r];
+        for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(outb + r * NS) * es] = v[q * R + r];
       }
     }
-    __syncthreads();
+    if (WARP_LOCAL) __syncwarp(); else __syncthreads();
   }
 }
 
 // Terminate the recursion at S == number of stages.
-template <int N, int S, bool LF, bool Done = (S >= fft_nstages(N))>
+template <int N, int S, bool LF, bool PAD = false, bool Done = (S >= fft_nstages(N))>
 struct FftRun {
   __device__ static __forceinline__ void run(float2* buf, int es, int ls, int nl, const float2* tw) {
-    fft_stage<N, S, LF>(buf, es, ls, nl, tw);
-    FftRun<N, S + 1, LF>::run(buf, es, ls, nl, tw);
+    fft_stage<N, S, LF, PAD>(buf, es, ls, nl, tw);
+    FftRun<N, S + 1, LF, PAD>::run(buf, es, ls, nl, tw);
   }
 };
-template <int N, int S, bool LF>
-struct FftRun<N, S, LF, true> {
+template <int N, int S, bool LF, bool PAD>
+struct FftRun<N, S, LF, PAD, true> {
+  __device__ static __forceinline__ void run(float2*, int, int, int, const float2*) {}
+};
+
+// Last stage into registers: stages 0 .. S-2 must already have run on the lines.
+// Each thread loads its butterfly inputs from the line lp, applies twiddles and the
+// DFT, and keeps the outputs: v[q * R + r] is element (tl + q * TPL) + r * (N / R).
+template <int N, bool LF, bool PAD>
+__device__ __forceinline__ void fft_last_stage_regs(const float2* lp, int es, int tl, const float2* tw,
+                                                    float2 (&v)[LF ? fft_elems_lf(N) : fft_elems(N)]) {
+  constexpr int S = fft_nstages(N) - 1;
+  constexpr int R = fft_radix(N, S);
+  constexpr int E = LF ? fft_elems_lf(N) : fft_elems(N);
+  constexpr int TPL = N / E;
+  constexpr int NB = E / R;
+  constexpr int NS = fft_ns_before(N, S);
+  constexpr int STRIDE = N / R;
+  constexpr int TWS = N / (NS * R);
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int j = tl + q * TPL;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q * R + r] = lp[fft_pos<PAD>(j + r * STRIDE) * es];
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int j = tl + q * TPL;
+    const int k = j % NS;
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tw[r * k * TWS]);
+    }
+    Dft<R>::run(&v[q * R]);
+  }
+}
+
+// First stage from registers: the caller holds, for its butterflies q < E/R0, the
+// inputs v[q * R0 + r] = x[fft_in_index<N>(tl, q, r)] of one line; this does the
+// stage-0 butterflies (no twiddles: N_s = 1) and stores the results to the line lp.
+// The remaining stages run with FftRun<N, 1, LF> after a __syncthreads().
+template <int N>
+__host__ __device__ constexpr int fft_in_index(int tl, int q, int r) {
+  return tl + q * (N / fft_elems(N)) + r * (N / fft_radix(N, 0));
+}
+
+template <int N, bool PAD>
+__device__ __forceinline__ void fft_stage0_regs(float2 (&v)[fft_elems(N)], float2* lp, int es, int tl) {
+  constexpr int R = fft_radix(N, 0);
+  constexpr int E = fft_elems(N);
+  constexpr int TPL = N / E;
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    Dft<R>::run(&v[q * R]);
+    const int j = tl + q * TPL;
+#pragma unroll
+    for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(j * R + r) * es] = v[q * R + r];
+  }
+}
+
+// Stages [S, END) only.
+template <int N, int S, int END, bool LF, bool PAD, bool Done = (S >= END)>
+struct FftRunTo {
+  __device__ static __forceinline__ void run(float2* buf, int es, int ls, int nl, const float2* tw) {
+    fft_stage<N, S, LF, PAD>(buf, es, ls, nl, tw);
+    FftRunTo<N, S + 1, END, LF, PAD>::run(buf, es, ls, nl, tw);
+  }
+};
+template <int N, int S, int END, bool LF, bool PAD>
+struct FftRunTo<N, S, END, LF, PAD, true> {
   __device__ static __forceinline__ void run(float2*, int, int, int, const float2*) {}
 };
 
 // In-place forward FFT of nl lines held in shared memory.  Every thread of the block
-// must call it (it contains __syncthreads).  blockDim.x must be >= N / E.
-template <int N, bool LF>
+// must call it.  blockDim.x must be >= N / E.  When a line is local to one warp the
+// stages only synchronise the warp: callers reading other warps' lines afterwards
+// need a __syncthreads() first.
+template <int N, bool LF, bool PAD = false>
 __device__ __forceinline__ void fft_smem(float2* buf, int es, int ls, int nl, const float2* tw) {
-  FftRun<N, 0, LF>::run(buf, es, ls, nl, tw);
+  FftRun<N, 0, LF, PAD>::run(buf, es, ls, nl, tw);
 }
 
 }  // namespace ys

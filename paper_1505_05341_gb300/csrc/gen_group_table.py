@@ -92,26 +92,44 @@ def emit(ell_max):
     lines.append(f"template <> struct GroupTable<{ell_max}> {{")
     lines.append(f"  static constexpr int NB = {nb};")
     lines.append(f"  static constexpr int NG = {ng};")
-    lines.append("  __device__ static __forceinline__ void combine(const float2 (&psi)[NB], float ky, float kz, float2 (&g)[NG]) {")
-    monos = sorted({m for poly in tab.values() for m in poly})
+    lines.append("  // G_g(k_y, k_z) = sum_beta poly_{g,beta}(k_y, k_z) Psi_beta; psi(beta) reads Psi_beta.")
+    lines.append("  template <class PsiAt>")
+    lines.append("  __device__ static __forceinline__ void combine(PsiAt psi, float ky, float kz, float2 (&g)[NG]) {")
     lines.append("    float kyp[5], kzp[5];")
     lines.append("    kyp[0] = 1.f; kzp[0] = 1.f;")
     lines.append("    #pragma unroll")
     lines.append("    for (int i = 1; i < 5; ++i) { kyp[i] = kyp[i - 1] * ky; kzp[i] = kzp[i - 1] * kz; }")
     for gi in range(ng):
         lines.append(f"    g[{gi}] = make_float2(0.f, 0.f);")
+    by_beta = {}
     for (gi, beta), poly in sorted(tab.items()):
-        terms = []
-        for (b, c), v in sorted(poly.items()):
-            assert v.denominator == 1
-            terms.append(f"({float(v.numerator)!r}f * kyp[{b}] * kzp[{c}])")
-        lines.append(f"    {{ const float w = {' + '.join(terms)};")
-        lines.append(f"      g[{gi}].x = fmaf(w, psi[{beta}].x, g[{gi}].x); g[{gi}].y = fmaf(w, psi[{beta}].y, g[{gi}].y); }}")
+        by_beta.setdefault(beta, []).append((gi, poly))
+    for beta in sorted(by_beta):
+        lines.append(f"    {{ const float2 ps = psi({beta});")
+        for gi, poly in by_beta[beta]:
+            terms = []
+            for (b, c), v in sorted(poly.items()):
+                assert v.denominator == 1
+                terms.append(f"({float(v.numerator)!r}f * kyp[{b}] * kzp[{c}])")
+            lines.append(f"      {{ const float w = {' + '.join(terms)};")
+            lines.append(f"        g[{gi}].x = fmaf(w, ps.x, g[{gi}].x); g[{gi}].y = fmaf(w, ps.y, g[{gi}].y); }}")
+        lines.append("    }")
     lines.append("  }")
-    # basis monomials for the field builder
-    lines.append("  // (a, b, c, degree) per basis field; degree 0 = F, -1 = F with the r = 0 node removed")
-    arr = ", ".join(f"{{{a}, {b}, {c}, {d}}}" for a, b, c, d in bs)
-    lines.append(f"  static constexpr int MONO[NB][4] = {{{arr}}};")
+    arr = ", ".join(f"{a}, {b}, {c}, {d}" for a, b, c, d in bs)
+    lines.append("  // mono_c(beta, i): i = 0, 1, 2 exponents of r_hat_x, r_hat_y, r_hat_z; i = 3 degree.")
+    lines.append("  __host__ __device__ static constexpr int mono_c(int beta, int i) {")
+    lines.append(f"    constexpr int t[{4 * nb}] = {{{arr}}};")
+    lines.append("    return t[4 * beta + i];")
+    lines.append("  }")
+    lines.append("  // Exponents (a, b, c) of r_hat_x^a r_hat_y^b r_hat_z^c and the degree of basis field")
+    lines.append("  // beta; degree 0 = F itself, -1 = F with the node at r = 0 removed.")
+    lines.append("  __device__ static __forceinline__ void mono(int beta, int& a, int& b, int& c, int& d) {")
+    lines.append("    switch (beta) {")
+    for i, (a, b, c, d) in enumerate(bs):
+        lines.append(f"      case {i}: a = {a}; b = {b}; c = {c}; d = {d}; break;")
+    lines.append("      default: a = 0; b = 0; c = 0; d = -2; break;")
+    lines.append("    }")
+    lines.append("  }")
     lines.append("};")
     return "\n".join(lines)
 

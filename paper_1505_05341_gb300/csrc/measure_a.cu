@@ -2,7 +2,15 @@
 #include "measure_impl.cuh"
 namespace ys {
 template cudaError_t run_measure_n<16>(Plan&);
+template int yz_grid_n<16>(int, cudaError_t*);
+template int x_pencils_n<16>();
 template cudaError_t run_measure_n<32>(Plan&);
+template int yz_grid_n<32>(int, cudaError_t*);
+template int x_pencils_n<32>();
 template cudaError_t run_measure_n<64>(Plan&);
+template int yz_grid_n<64>(int, cudaError_t*);
+template int x_pencils_n<64>();
 template cudaError_t run_measure_n<96>(Plan&);
+template int yz_grid_n<96>(int, cudaError_t*);
+template int x_pencils_n<96>();
 }  // namespace ys

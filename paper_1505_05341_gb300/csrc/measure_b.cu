@@ -2,5 +2,9 @@
 #include "measure_impl.cuh"
 namespace ys {
 template cudaError_t run_measure_n<128>(Plan&);
+template int yz_grid_n<128>(int, cudaError_t*);
+template int x_pencils_n<128>();
 template cudaError_t run_measure_n<192>(Plan&);
+template int yz_grid_n<192>(int, cudaError_t*);
+template int x_pencils_n<192>();
 }  // namespace ys

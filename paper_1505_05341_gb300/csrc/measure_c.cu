@@ -2,5 +2,9 @@
 #include "measure_impl.cuh"
 namespace ys {
 template cudaError_t run_measure_n<256>(Plan&);
+template int yz_grid_n<256>(int, cudaError_t*);
+template int x_pencils_n<256>();
 template cudaError_t run_measure_n<384>(Plan&);
+template int yz_grid_n<384>(int, cudaError_t*);
+template int x_pencils_n<384>();
 }  // namespace ys

@@ -2,4 +2,6 @@
 #include "measure_impl.cuh"
 namespace ys {
 template cudaError_t run_measure_n<512>(Plan&);
+template int yz_grid_n<512>(int, cudaError_t*);
+template int x_pencils_n<512>();
 }  // namespace ys

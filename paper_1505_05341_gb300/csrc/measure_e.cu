@@ -2,5 +2,9 @@
 #include "measure_impl.cuh"
 namespace ys {
 template cudaError_t run_measure_n<768>(Plan&);
+template int yz_grid_n<768>(int, cudaError_t*);
+template int x_pencils_n<768>();
 template cudaError_t run_measure_n<1024>(Plan&);
+template int yz_grid_n<1024>(int, cudaError_t*);
+template int x_pencils_n<1024>();
 }  // namespace ys

@@ -9,53 +9,82 @@ namespace ys {
 
 cudaError_t launch_finalize(Plan& p);
 
+// CTAs of the persistent y,z kernel that fit on the device at once.
+template <int N, int ELL>
+int yz_grid(cudaError_t* err) {
+  using Y = YZ<N, ELL>;
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!e) e = cudaFuncSetAttribute(k_yz<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem);
+  if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_yz<N, ELL>, Y::THREADS, Y::smem);
+  if (err) *err = e;
+  return e ? 0 : std::max(1, per) * sms;
+}
+
+template <int N>
+int yz_grid_n(int ell, cudaError_t* err) {
+  switch (ell) {
+    case 0: return yz_grid<N, 0>(err);
+    case 2: return yz_grid<N, 2>(err);
+    default: return yz_grid<N, 4>(err);
+  }
+}
+
 template <int N, int ELL>
 cudaError_t run_yz(Plan& p) {
-  using T = GroupTable<ELL>;
-  cudaStream_t st = p.stream;
+  using Y = YZ<N, ELL>;
   cudaError_t err;
-  const size_t smem_rows = sizeof(float2) * N + sizeof(float2) * KZ_ROWS * (N + 1) + sizeof(float) * KZ_ROWS * N;
-  const int kc = std::max(1, std::min(p.nzc, (int)(98304 / (T::NB * (N + 1) * sizeof(float2)))));
-  const size_t smem_cols = sizeof(float2) * N + sizeof(float2) * T::NB * kc * (N + 1);
-  if ((err = cudaFuncSetAttribute(k_yz_rows<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows)))
+  if ((err = cudaMemsetAsync(p.d_sync, 0, sizeof(int) * (2 * p.m * N + 2), p.stream))) return err;
+  YZParams prm;
+  prm.mesh = p.d_mesh;
+  prm.rel = p.d_rel;
+  prm.tw = p.d_tw;
+  prm.ring = p.d_z;
+  prm.gout = p.d_g;
+  prm.col_off = p.d_col_off;
+  prm.done_z = p.d_sync;
+  prm.done_y = p.d_sync + p.m * N;
+  prm.ticket = p.d_sync + 2 * p.m * N;
+  prm.err = p.d_sync + 2 * p.m * N + 1;
+  prm.nzc = p.nzc;
+  prm.np = p.np_pad;
+  prm.m = p.m;
+  prm.S = p.ring_slots;
+  prm.D = p.ring_lead;
+  prm.spin_limit = 4000000;  // ~1 s of 128 ns sleeps, then the kernel reports a timeout
+  if ((err = cudaFuncSetAttribute(k_yz<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem)))
     return err;
-  if ((err = cudaFuncSetAttribute(k_yz_cols<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols)))
-    return err;
-  const size_t n3 = (size_t)N * N * N;
-  for (int mj = 0; mj < p.m; ++mj) {
-    const float* rel = p.d_rel + (size_t)mj * 3 * N;
-    for (int ix0 = 0; ix0 < N; ix0 += p.batch) {
-      const int nb = std::min(p.batch, N - ix0);
-      {
-        LaunchScope ls(p, 4);
-        k_yz_rows<N, ELL><<<dim3(N / KZ_ROWS, nb), KZ_THREADS, smem_rows, st>>>(
-          p.d_mesh + mj * n3, ix0, rel, rel + N, rel + 2 * N, p.d_tw, p.d_z, p.nzc, p.batch);
-        if ((err = cudaGetLastError())) return err;
-      }
-      LaunchScope ls(p, 5);
-      k_yz_cols<N, ELL><<<dim3((p.nzc + kc - 1) / kc, nb), KY_THREADS, smem_cols, st>>>(
-          p.d_z, ix0, p.nzc, p.batch, kc, p.d_col_off, p.d_tw, p.d_g, mj, p.np);
-      if ((err = cudaGetLastError())) return err;
-    }
-  }
-  return cudaSuccess;
+  LaunchScope ls(p, 4);
+  k_yz<N, ELL><<<p.yz_grid, Y::THREADS, Y::smem, p.stream>>>(prm);
+  return cudaGetLastError();
 }
 
 template <int N, int ELL, int M>
 cudaError_t run_x(Plan& p) {
   using XC = XCombine<N, ELL, M>;
   const int nbins = p.cfg.n_bins;
-  const size_t smem = x_combine_smem<N, ELL, M>(nbins);
+  const size_t smem = XC::smem(nbins);
   cudaError_t err;
   if ((err = cudaFuncSetAttribute(k_x_combine<N, ELL, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return err;
-  const int npb = (p.np + XC::P - 1) / XC::P;
-  const int grid = std::max(1, std::min(npb, 152 * 4));
+  int dev = 0, sms = 0, per = 0;
+  if ((err = cudaGetDevice(&dev))) return err;
+  if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_x_combine<N, ELL, M>, XC::THREADS, smem)))
+    return err;
+  const int npb = p.np_pad / XC::P;
+  const int grid = std::max(1, std::min(npb, std::max(1, per) * sms));
   LaunchScope ls(p, 6);
-  k_x_combine<N, ELL, M><<<grid, XC::THREADS, smem, p.stream>>>(p.d_g, p.np, p.d_pencil, p.d_tw, p.d_invw,
-                                                                 p.d_phase, p.d_lut, p.n2_hi, p.d_acc, nbins);
+  k_x_combine<N, ELL, M><<<grid, XC::THREADS, smem, p.stream>>>(p.gmap, p.np_pad, p.d_pencil, p.d_tw, p.d_invw,
+                                                                 p.d_phase, p.d_lut, p.n2_hi, p.d_acc, nbins,
+                                                                 p.d_sync + 2 * p.m * N + 1);
   return cudaGetLastError();
 }
+
+// Pencils per x-stage CTA for mesh size N (for the host-side padding).
+template <int N>
+int x_pencils_n() { return k3_pencils(N); }
 
 template <int N, int ELL>
 cudaError_t run_ell(Plan& p) {

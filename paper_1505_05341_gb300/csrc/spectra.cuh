@@ -19,7 +19,10 @@
 //             shared and global accumulators).
 //  k_finalize   alpha, I, S and Eqs. (6)-(8) per shell.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "fft.cuh"
 #include "ys_internal.h"
@@ -28,10 +31,6 @@ namespace ys {
 
 #include "group_table.inc"
 
-// Rows per CTA in k_yz_rows and pencils per CTA in k_x_combine.
-constexpr int KZ_ROWS = 16;
-constexpr int KZ_THREADS = 256;
-constexpr int KY_THREADS = 256;
 
 template <int A>
 __device__ __forceinline__ float ipow(float v) {
@@ -41,132 +40,276 @@ __device__ __forceinline__ float ipow(float v) {
   return r;
 }
 
-// Value of basis field `beta` at one node.
+// Value of basis field BETA at one node (compile-time exponents; 0 past the last field).
 template <int ELL, int BETA>
 __device__ __forceinline__ float basis_value(float f, float xh, float yh, float zh, bool nonzero_r) {
-  using T = GroupTable<ELL>;
-  if constexpr (BETA >= T::NB) {
+  if constexpr (BETA >= GroupTable<ELL>::NB) {
     return 0.f;
   } else {
-    constexpr int a = T::MONO[BETA][0], b = T::MONO[BETA][1], c = T::MONO[BETA][2], d = T::MONO[BETA][3];
+    constexpr int a = GroupTable<ELL>::mono_c(BETA, 0), b = GroupTable<ELL>::mono_c(BETA, 1);
+    constexpr int c = GroupTable<ELL>::mono_c(BETA, 2), d = GroupTable<ELL>::mono_c(BETA, 3);
     if constexpr (d == 0) return f;
     else if constexpr (d == -1) return nonzero_r ? f : 0.f;
-    else return f * ipow<a>(xh) * ipow<b>(yh) * ipow<c>(zh);
-  }
-}
-
-template <int N, int ELL, int PAIR>
-__device__ __forceinline__ void fill_pair(float2* C, const float* Fs, float X, const float* __restrict__ rely,
-                                          const float* __restrict__ relz, int row0) {
-  for (int e = threadIdx.x; e < KZ_ROWS * N; e += blockDim.x) {
-    const int r = e / N, z = e - (e / N) * N;
-    const float Y = rely[row0 + r], Z = relz[z];
-    const float f = Fs[e];
-    const float r2 = fmaf(X, X, fmaf(Y, Y, Z * Z));
-    const bool nz = r2 > 0.f;
-    const float rinv = nz ? rsqrtf(r2) : 0.f;
-    const float xh = X * rinv, yh = Y * rinv, zh = Z * rinv;
-    C[r * (N + 1) + z] = make_float2(basis_value<ELL, 2 * PAIR>(f, xh, yh, zh, nz),
-                                     basis_value<ELL, 2 * PAIR + 1>(f, xh, yh, zh, nz));
-  }
-}
-
-template <int N, int ELL, int PAIR>
-__device__ __forceinline__ void split_store(const float2* C, float2* __restrict__ zbuf, int slot, int batch,
-                                            int nzc, int row0) {
-  constexpr int NB = GroupTable<ELL>::NB;
-  constexpr int FA = 2 * PAIR, FB = 2 * PAIR + 1;
-  for (int e = threadIdx.x; e < nzc * KZ_ROWS; e += blockDim.x) {
-    const int kz = e / KZ_ROWS, r = e - kz * KZ_ROWS;
-    const float2 ck = C[r * (N + 1) + kz];
-    const float2 cm = C[r * (N + 1) + (kz == 0 ? 0 : N - kz)];
-    // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i).
-    const float2 A = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
-    zbuf[(((size_t)FA * batch + slot) * nzc + kz) * N + row0 + r] = A;
-    if constexpr (FB < NB) {
-      const float2 B = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
-      zbuf[(((size_t)FB * batch + slot) * nzc + kz) * N + row0 + r] = B;
+    else {
+      float v = f;
+#pragma unroll
+      for (int i = 0; i < a; ++i) v *= xh;
+#pragma unroll
+      for (int i = 0; i < b; ++i) v *= yh;
+#pragma unroll
+      for (int i = 0; i < c; ++i) v *= zh;
+      return v;
     }
   }
 }
 
-template <int N, int ELL, int PAIR>
-struct PairLoop {
-  __device__ static __forceinline__ void run(float2* C, const float* Fs, float X, const float* rely,
-                                             const float* relz, int row0, const float2* tw, float2* zbuf,
-                                             int slot, int batch, int nzc) {
-    constexpr int NB = GroupTable<ELL>::NB;
-    if constexpr (2 * PAIR < NB) {
-      fill_pair<N, ELL, PAIR>(C, Fs, X, rely, relz, row0);
-      __syncthreads();
-      fft_smem<N, false>(C, 1, N + 1, KZ_ROWS, tw);
-      split_store<N, ELL, PAIR>(C, zbuf, slot, batch, nzc, row0);
-      __syncthreads();
-      PairLoop<N, ELL, PAIR + 1>::run(C, Fs, X, rely, relz, row0, tw, zbuf, slot, batch, nzc);
-    }
-  }
+// ---------------------------------------------------------------------------
+// y,z stage: one persistent kernel over a ticketed work list.
+//
+// Planes p = 0 .. m N - 1 (mesh j = p / N, x index p % N).  Per plane there are NZ
+// "row items" (R rows of the plane: the basis fields, complex FFTs of two real
+// fields along z, the split into the two half spectra for k_z < nzc, written to a
+// ring slot laid out [field][k_z][y]) and NY = nzc "column items" (one k_z column:
+// FFT along y of every basis field, the k_y, k_z polynomial fold into the k_x-power
+// groups, written for the pencils of that column).  Tickets are handed out in steps:
+// step t = row items of plane t, then column items of plane t - D.  Row items of
+// plane p reuse ring slot p mod S once the column items of plane p - S are done;
+// column items of plane p start once its row items are done.  Both waits are on
+// per-plane completion counters (release / acquire), bounded in time; a CTA only
+// ever waits on items claimed before its own, so the list cannot deadlock.
+// ---------------------------------------------------------------------------
+
+struct YZParams {
+  const float* mesh;     // [m][N][N][N]
+  const float* rel;      // [m][3][N] node - observer
+  const float2* tw;      // [N]
+  float2* ring;          // [S][NB][nzc][N]
+  float2* gout;          // [m][NG][N][np]
+  const int* col_off;    // [nzc + 1]
+  int* done_z;           // [m N]
+  int* done_y;           // [m N]
+  int* ticket;           // [1]
+  int* err;              // [1]
+  int nzc, np, m, S, D;
+  long long spin_limit;
 };
 
-template <int N, int ELL>
-__global__ void __launch_bounds__(KZ_THREADS)
-k_yz_rows(const float* __restrict__ mesh, int ix0, const float* __restrict__ relx, const float* __restrict__ rely,
-          const float* __restrict__ relz, const float2* __restrict__ tw_g, float2* __restrict__ zbuf, int nzc,
-          int batch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* C = tw + N;
-  float* Fs = reinterpret_cast<float*>(C + KZ_ROWS * (N + 1));
-  const int slot = blockIdx.y;
-  const int ix = ix0 + slot;
-  const int row0 = blockIdx.x * KZ_ROWS;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
-  const float* src = mesh + ((size_t)ix * N + row0) * N;
-  for (int k = threadIdx.x; k < KZ_ROWS * N / 4; k += blockDim.x)
-    reinterpret_cast<float4*>(Fs)[k] = reinterpret_cast<const float4*>(src)[k];
+template <int N>
+__host__ __device__ constexpr int yz_rows() { return N >= 512 ? 8 : 16; }
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits until *addr >= target; false (and the error flag set) on timeout
+// or when another CTA has already failed.
+__device__ __forceinline__ bool wait_geq(const int* addr, int target, int* err, long long limit) {
+  long long it = 0;
+  while (ld_acquire(addr) < target) {
+    if (++it > limit) {
+      atomicExch(err, 1);
+      return false;
+    }
+    if ((it & 31) == 0 && *reinterpret_cast<volatile int*>(err)) return false;
+    __nanosleep(128);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void signal_done(int* counter) {
+  __threadfence();
   __syncthreads();
-  PairLoop<N, ELL, 0>::run(C, Fs, relx[ix], rely, relz, row0, tw, zbuf, slot, batch, nzc);
+  if (threadIdx.x == 0) atomicAdd(counter, 1);
 }
 
 template <int N, int ELL>
-__global__ void __launch_bounds__(KY_THREADS)
-k_yz_cols(const float2* __restrict__ zbuf, int ix0, int nzc, int batch, int kc, const int* __restrict__ col_off,
-          const float2* __restrict__ tw_g, float2* __restrict__ gout, int mesh_j, int np) {
+struct YZ {
   using T = GroupTable<ELL>;
-  constexpr int NB = T::NB, NG = T::NG;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* S = tw + N;
-  const int slot = blockIdx.y;
-  const int ix = ix0 + slot;
-  const int kz0 = blockIdx.x * kc;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
-  const int nl = NB * kc;
-  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
-    const int line = e / N, iy = e - (e / N) * N;
-    const int f = line / kc, c = line - f * kc;
-    const int kz = kz0 + c;
-    S[line * (N + 1) + iy] =
-        kz < nzc ? zbuf[(((size_t)f * batch + slot) * nzc + kz) * N + iy] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_smem<N, false>(S, 1, N + 1, nl, tw);
-  for (int c = 0; c < kc; ++c) {
-    const int kz = kz0 + c;
-    if (kz >= nzc) break;
-    const int p0 = col_off[kz];
-    const int cnt = col_off[kz + 1] - p0;
-    const int kymax = (cnt - 1) / 2;
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-      const int ky = q - kymax;
-      const int iyk = ky < 0 ? ky + N : ky;
-      float2 psi[NB];
+  static constexpr int NB = T::NB, NG = T::NG, NPAIR = (NB + 1) / 2;
+  static constexpr int E = fft_elems(N), TPL = N / E;
+  static constexpr int R0 = fft_radix(N, 0);
+  static constexpr int THREADS = 256;
+  static constexpr int LPP = THREADS / TPL;                  // lines per pass
+  static constexpr bool WARP_LOCAL = TPL <= 32;
+  static constexpr int R0WS = (N >= 512 ? 8 : 16);
+  static constexpr int R = (LPP > R0WS ? (LPP < N ? LPP : N) : R0WS);  // rows per row item
+  static constexpr int PASSES = (R + LPP - 1) / LPP;
+  static constexpr int LL = fft_line_len<N, true>();         // padded line length
+  static constexpr size_t smem_z = sizeof(float2) * 2 * R * LL;
+  static constexpr size_t smem_y = sizeof(float2) * NB * LL;
+  static constexpr size_t smem = sizeof(float2) * N + (smem_z > smem_y ? smem_z : smem_y);
+  static_assert(N % R == 0, "rows per item must divide N");
+};
+
+template <int N>
+__device__ __forceinline__ void line_sync() {
+  if constexpr (N / fft_elems(N) <= 32) __syncwarp(); else __syncthreads();
+}
+
+// One pair of basis fields for the R rows of a row item: fields at the nodes (first
+// FFT stage from registers), FFT along z, then the split of the two real fields into
+// their half spectra, written to the ring slot.  C is one of two line buffers, so
+// the split of this pair can overlap the FFT of the next.
+template <int N, int ELL, int PAIR>
+__device__ __noinline__ void row_pair(float2* C, const float* __restrict__ plane, float X,
+                                         const float* __restrict__ rely, const float* __restrict__ relz, int row0,
+                                         const float2* tw, float2* __restrict__ zslot, int nzc) {
+  using Y = YZ<N, ELL>;
+  constexpr int E = Y::E, TPL = Y::TPL, R0 = Y::R0, R = Y::R, NB = Y::NB, LL = Y::LL, LPP = Y::LPP;
+  const int tl = threadIdx.x % TPL;
 #pragma unroll
-      for (int f = 0; f < NB; ++f) psi[f] = S[(f * kc + c) * (N + 1) + iyk];
-      float2 g[NG];
-      T::combine(psi, (float)ky, (float)kz, g);
+  for (int ps = 0; ps < Y::PASSES; ++ps) {
+    const int row = ps * LPP + threadIdx.x / TPL;
+    if (row < R) {
+      const float Yc = rely[row0 + row];
+      float2 v[E];
 #pragma unroll
-      for (int gi = 0; gi < NG; ++gi) gout[(((size_t)mesh_j * NG + gi) * N + ix) * np + p0 + q] = g[gi];
+      for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int z = fft_in_index<N>(tl, q, r);
+          const float Zc = relz[z];
+          const float f = plane[(size_t)(row0 + row) * N + z];
+          const float r2 = fmaf(X, X, fmaf(Yc, Yc, Zc * Zc));
+          const bool nz = r2 > 0.f;
+          const float rinv = nz ? rsqrtf(r2) : 0.f;
+          const float xh = X * rinv, yh = Yc * rinv, zh = Zc * rinv;
+          v[q * R0 + r] = make_float2(basis_value<ELL, 2 * PAIR>(f, xh, yh, zh, nz),
+                                      basis_value<ELL, 2 * PAIR + 1>(f, xh, yh, zh, nz));
+        }
+      fft_stage0_regs<N, true>(v, C + row * LL, 1, tl);
     }
+  }
+  line_sync<N>();
+  FftRun<N, 1, false, true>::run(C, 1, LL, R, tw);
+  __syncthreads();
+  constexpr int FA = 2 * PAIR, FB = 2 * PAIR + 1;
+  for (int e = threadIdx.x; e < nzc * R; e += blockDim.x) {
+    const int kz = e / R, r = e - kz * R;
+    const float2 ck = C[r * LL + fft_pos<true>(kz)];
+    const float2 cm = C[r * LL + fft_pos<true>(kz == 0 ? 0 : N - kz)];
+    // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i).
+    zslot[((size_t)FA * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
+    if constexpr (FB < NB)
+      zslot[((size_t)FB * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
+  }
+}
+
+template <int N, int ELL>
+__device__ __noinline__ void row_item(float2* work, const float* __restrict__ plane, float X,
+                                         const float* __restrict__ rely, const float* __restrict__ relz, int row0,
+                                         const float2* tw, float2* __restrict__ zslot, int nzc) {
+  using Y = YZ<N, ELL>;
+  constexpr int E = Y::E, TPL = Y::TPL, R0 = Y::R0, R = Y::R, LL = Y::LL, LPP = Y::LPP;
+#pragma unroll 1
+  for (int pr = 0; pr < Y::NPAIR; ++pr) {
+    float2* C = work + (pr & 1) * R * LL;
+    switch (pr) {
+      case 0: row_pair<N, ELL, 0>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      case 1: row_pair<N, ELL, 1>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      case 2: row_pair<N, ELL, 2>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      case 3: row_pair<N, ELL, 3>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      case 4: row_pair<N, ELL, 4>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      case 5: row_pair<N, ELL, 5>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      case 6: row_pair<N, ELL, 6>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+      default: row_pair<N, ELL, 7>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
+    }
+  }
+}
+
+template <int N, int ELL>
+__device__ __noinline__ void column_fold(const float2* S, int kz, const int* __restrict__ col_off,
+                                         float2* __restrict__ gout, int j, int ix, int np) {
+  using Y = YZ<N, ELL>;
+  constexpr int NG = Y::NG, LL = Y::LL;
+  const int p0 = col_off[kz];
+  const int cnt = col_off[kz + 1] - p0;
+  const int kymax = (cnt - 1) / 2;
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int ky = q - kymax;
+    const int pos = fft_pos<true>(ky < 0 ? ky + N : ky);
+    float2 g[NG];
+    GroupTable<ELL>::combine([&](int f) { return S[f * LL + pos]; }, (float)ky, (float)kz, g);
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) gout[(((size_t)j * NG + gi) * N + ix) * np + p0 + q] = g[gi];
+  }
+}
+
+template <int N, int ELL>
+__device__ __noinline__ void column_item(float2* S, const float2* __restrict__ zs, int nzc, int kz,
+                                            const int* __restrict__ col_off, const float2* tw,
+                                            float2* __restrict__ gout, int j, int ix, int np) {
+  using Y = YZ<N, ELL>;
+  constexpr int NB = Y::NB, E = Y::E, TPL = Y::TPL, R0 = Y::R0, LL = Y::LL, LPP = Y::LPP;
+  const int tl = threadIdx.x % TPL;
+  for (int base = 0; base < NB; base += LPP) {
+    const int f = base + threadIdx.x / TPL;
+    if (f < NB) {
+      const float2* line = zs + ((size_t)f * nzc + kz) * N;
+      float2 v[E];
+#pragma unroll
+      for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[q * R0 + r] = __ldcg(line + fft_in_index<N>(tl, q, r));
+      fft_stage0_regs<N, true>(v, S + f * LL, 1, tl);
+    }
+  }
+  line_sync<N>();
+  FftRun<N, 1, false, true>::run(S, 1, LL, NB, tw);
+  __syncthreads();
+  column_fold<N, ELL>(S, kz, col_off, gout, j, ix, np);
+}
+
+template <int N, int ELL>
+__global__ void __launch_bounds__(256, (N >= 1024 ? 1 : 2)) k_yz(YZParams prm) {
+  using Y = YZ<N, ELL>;
+  constexpr int R = Y::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  __shared__ int s_ok;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* work = tw + N;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = prm.tw[k];
+  const int NZ = N / R, NY = prm.nzc, IPS = NZ + NY;
+  const int mN = prm.m * N;
+  const int total = (mN + prm.D) * IPS;
+  const size_t n3 = (size_t)N * N * N;
+  const size_t slot_elems = (size_t)Y::NB * prm.nzc * N;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(prm.ticket, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int step = item / IPS, sub = item - step * IPS;
+    if (sub < NZ) {
+      const int p = step;  // row item of plane p
+      if (p < mN) {
+        if (threadIdx.x == 0)
+          s_ok = (p < prm.S) ? 1 : (int)wait_geq(prm.done_y + (p - prm.S), NY, prm.err, prm.spin_limit);
+        __syncthreads();
+        if (!s_ok) break;
+        const int j = p / N, ix = p - j * N;
+        const float* rel = prm.rel + (size_t)j * 3 * N;
+        row_item<N, ELL>(work, prm.mesh + j * n3 + (size_t)ix * N * N, rel[ix], rel + N, rel + 2 * N, sub * R, tw,
+                         prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc);
+        signal_done(prm.done_z + p);
+      }
+    } else {
+      const int p = step - prm.D;  // column item of plane p
+      if (p >= 0) {
+        if (threadIdx.x == 0) s_ok = (int)wait_geq(prm.done_z + p, NZ, prm.err, prm.spin_limit);
+        __syncthreads();
+        if (!s_ok) break;
+        const int j = p / N, ix = p - j * N;
+        column_item<N, ELL>(work, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc, sub - NZ, prm.col_off, tw,
+                            prm.gout, j, ix, prm.np);
+        signal_done(prm.done_y + p);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -193,126 +336,218 @@ __device__ __forceinline__ bool warp_segment_sum(float& v, int key) {
 // Pencils per CTA of k_x_combine.
 __host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 1024 ? 4 : 8); }
 
+// ---------------------------------------------------------------------------
+// x stage: FFT along x of every (mesh, group) tile of P pencils, fed by TMA.
+// The grouped y,z transforms are a 2D tensor [m NG N rows][np_pad pencils] of
+// float2; one tile (all N rows x P pencils) arrives by BOXES 2D bulk-tensor copies
+// into one of two shared buffers (mbarrier completion), so the copy of the next
+// tile overlaps the FFT of this one.  The last FFT stage stays in registers: each
+// thread owns E modes (one pencil, E values of k_x) for the whole pencil block and
+// accumulates A_0 and k^n A_n there; the per-mode terms of the shell sums go to
+// per-warp float bins in shared memory, folded into FP64 bins per pencil block.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for the given phase parity of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 template <int N, int ELL, int M>
 struct XCombine {
   static constexpr int P = k3_pencils(N);
-  static constexpr int E = fft_elems(N);
-  static constexpr int THREADS = P * (N / E);
+  static constexpr int E = fft_elems_lf(N);
+  static constexpr int TPL = N / E;
+  static constexpr int THREADS = P * TPL;
   static constexpr int NW = THREADS / 32;
-  static constexpr int ITEMS = P * N / 32;           // runs of 32 consecutive (pencil, k_x) modes
-  static constexpr int K = ITEMS / NW;               // modes per thread
+  static constexpr int NG = GroupTable<ELL>::NG;
+  static constexpr int TILES = NG * M;
+  static constexpr int BOX_ROWS = N < 256 ? N : 256;
+  static constexpr int BOXES = N / BOX_ROWS;
+  static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
+  static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
   static_assert(THREADS % 32 == 0, "threads");
-  static_assert(ITEMS % NW == 0, "items");
+  static size_t smem(int nbins) {
+    size_t b = 2 * (size_t)TILE_BYTES;                       // two tile buffers
+    b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
+    b += sizeof(float) * NW * 3 * nbins;                     // per-warp float bins
+    b = (b + 7) & ~size_t(7);
+    b += sizeof(double) * 3 * nbins;                         // per-CTA FP64 bins
+    return b + 128;                                          // alignment slack
+  }
 };
 
 template <int N, int ELL, int M>
 __global__ void __launch_bounds__(XCombine<N, ELL, M>::THREADS)
-k_x_combine(const float2* __restrict__ gin, int np, const short2* __restrict__ pencil, const float2* __restrict__ tw_g,
-            const float* __restrict__ invw_g, const float2* __restrict__ phase_g, const short* __restrict__ lut,
-            int n2_hi, double* __restrict__ acc, int nbins) {
+k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* __restrict__ pencil,
+            const float2* __restrict__ tw_g, const float* __restrict__ invw_g, const float2* __restrict__ phase_g,
+            const short* __restrict__ lut, int n2_hi, double* __restrict__ acc, int nbins, int* __restrict__ err) {
   using XC = XCombine<N, ELL, M>;
-  constexpr int P = XC::P, K = XC::K, NW = XC::NW, PP = P + 1;
-  constexpr int NG = GroupTable<ELL>::NG;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sbin = reinterpret_cast<double*>(smem_raw);                 // [3][nbins]
-  float2* tw = reinterpret_cast<float2*>(sbin + 3 * nbins);          // [N]
-  float2* phs = tw + N;                                              // [N]
-  float* invw = reinterpret_cast<float*>(phs + N);                   // [N]
-  short2* spen = reinterpret_cast<short2*>(invw + N);                // [P]
-  float2* T = reinterpret_cast<float2*>(spen + P + (P & 1));         // [N][P + 1]
-  for (int k = threadIdx.x; k < 3 * nbins; k += blockDim.x) sbin[k] = 0.0;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+  constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, NW = XC::NW, TILES = XC::TILES, RL = XC::RL;
+  constexpr int NBL = E / RL;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ int s_fail;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float2* T0 = reinterpret_cast<float2*>(base);
+  float2* tw = T0 + 2 * N * P;
+  float2* phs = tw + N;
+  float* invw = reinterpret_cast<float*>(phs + N);
+  float* wbin = invw + N;
+  double* cbin = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wbin + NW * 3 * nbins) + 7) & ~uintptr_t(7));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int k = tid; k < N; k += blockDim.x) {
     tw[k] = tw_g[k];
     phs[k] = phase_g[k];
     invw[k] = invw_g[k];
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int npb = (np + P - 1) / P;
-  for (int pb = blockIdx.x; pb < npb; pb += gridDim.x) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-      const int pi = pb * P + k;
-      spen[k] = pi < np ? pencil[pi] : make_short2(0, -1);
-    }
-    __syncthreads();
-    float2 a0[K], ga[K];
-    // A single pass over (mesh, group) tiles; groups are visited in order A_0, then
-    // the k_x powers of A_2, then those of A_4.
-    for (int gi = 0; gi < NG; ++gi) {
-      for (int mj = 0; mj < M; ++mj) {
-        const float2* src = gin + ((size_t)(mj * NG + gi) * N) * np + (size_t)pb * P;
-        for (int e = threadIdx.x; e < N * P; e += blockDim.x) {
-          const int ix = e / P, p = e - (e / P) * P;
-          T[ix * PP + p] = (pb * P + p < np) ? src[(size_t)ix * np + p] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        fft_smem<N, true>(T, PP, 1, P, tw);
-        const int pw = (gi == 0) ? 0 : (gi <= 3 ? gi - 1 : gi - 4);  // power of k_x
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-          const int flat = (warp + NW * q) * 32 + lane;
-          const int p = flat / N, kx = flat - (flat / N) * N;
-          const short2 pc = spen[p];
-          const int ky = pc.x, kz = pc.y;
-          const int mx = kx <= N / 2 ? kx : kx - N;
-          const int iyk = ky < 0 ? ky + N : ky;
-          float cf = invw[kx] * invw[iyk] * invw[kz < 0 ? 0 : kz] * (M == 2 ? 0.5f : 1.f);
-          float2 X = T[kx * PP + p];
-          if (M == 2 && mj == 1) {
-            const float2 ph = cmul(cmul(phs[kx], phs[iyk]), phs[kz < 0 ? 0 : kz]);
-            X = cmul(X, ph);
-          }
-          float kp = cf;
-          for (int t = 0; t < pw; ++t) kp *= (float)mx;
-          if (gi == 0) {
-            if (mj == 0) a0[q] = make_float2(kp * X.x, kp * X.y);
-            else { a0[q].x = fmaf(kp, X.x, a0[q].x); a0[q].y = fmaf(kp, X.y, a0[q].y); }
-          } else {
-            const bool first = (gi == 1 || gi == 4) && mj == 0;
-            if (first) ga[q] = make_float2(kp * X.x, kp * X.y);
-            else { ga[q].x = fmaf(kp, X.x, ga[q].x); ga[q].y = fmaf(kp, X.y, ga[q].y); }
-          }
-        }
-        __syncthreads();
-      }
-      // After the last tile of A_0, of A_2 (gi == 3) or of A_4 (gi == 8): shell sums.
-      const int slot = (gi == 0) ? 0 : (gi == 3 ? 1 : (gi == 8 ? 2 : -1));
-      if (slot >= 0) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-          const int flat = (warp + NW * q) * 32 + lane;
-          const int p = flat / N, kx = flat - (flat / N) * N;
-          const short2 pc = spen[p];
-          const int ky = pc.x, kz = pc.y;
-          const int mx = kx <= N / 2 ? kx : kx - N;
-          const int n2 = mx * mx + ky * ky + kz * kz;
-          int bin = -1;
-          if (kz >= 0 && n2 < n2_hi) bin = lut[n2];
-          const float wgt = (bin >= 0) ? (kz == 0 ? 1.f : 2.f) : 0.f;
-          float v;
-          if (slot == 0) {
-            v = wgt * (a0[q].x * a0[q].x + a0[q].y * a0[q].y);
-          } else {
-            const float inv = n2 > 0 ? 1.f / (float)n2 : 0.f;
-            const float invn = slot == 1 ? inv : inv * inv;
-            v = wgt * invn * (a0[q].x * ga[q].x + a0[q].y * ga[q].y);
-          }
-          if (warp_segment_sum(v, bin) && bin >= 0) atomicAdd(&sbin[slot * nbins + bin], (double)v);
-        }
-      }
-    }
+  for (int k = tid; k < NW * 3 * nbins; k += blockDim.x) wbin[k] = 0.f;
+  for (int k = tid; k < 3 * nbins; k += blockDim.x) cbin[k] = 0.0;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < 3 * nbins; k += blockDim.x)
-    if (sbin[k] != 0.0) atomicAdd(&acc[k], sbin[k]);
-}
-
-template <int N, int ELL, int M>
-size_t x_combine_smem(int nbins) {
-  constexpr int P = k3_pencils(N);
-  size_t b = sizeof(double) * 3 * nbins + sizeof(float2) * 2 * N + sizeof(float) * N + sizeof(short2) * (P + (P & 1));
-  b = (b + 15) & ~size_t(15);
-  return b + sizeof(float2) * N * (P + 1);
+  const int npb = np_pad / P;
+  const int mine = blockIdx.x < npb ? (npb - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int total = mine * TILES;
+  auto issue = [&](int s) {
+    const int k = s / TILES, t = s - k * TILES;
+    const int gi = t / M, mj = t - gi * M;
+    const int pb = blockIdx.x + k * gridDim.x;
+    float2* dst = T0 + (s & 1) * N * P;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[s & 1], XC::TILE_BYTES);
+#pragma unroll
+    for (int bx = 0; bx < XC::BOXES; ++bx)
+      tma_load_2d(dst + bx * XC::BOX_ROWS * P, &gmap, pb * P * 2, (mj * XC::NG + gi) * N + bx * XC::BOX_ROWS, &bar[s & 1]);
+  };
+  if (tid == 0 && total > 0) issue(0);
+  const int p = tid % P, tl = tid / P;
+  float2 a0[E], ga[E];
+  int ky = 0, kz = -1, iyk = 0;
+  float cf_pen = 0.f;
+  float2 ph_pen = make_float2(1.f, 0.f);
+  for (int s = 0; s < total; ++s) {
+    if (tid == 0 && s + 1 < total) issue(s + 1);
+    if (!mbar_wait(&bar[s & 1], (s >> 1) & 1, 1LL << 24)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) break;
+    const int k = s / TILES, t = s - k * TILES;
+    const int gi = t / M, mj = t - gi * M;
+    if (t == 0) {
+      const short2 pc = pencil[(blockIdx.x + k * gridDim.x) * P + p];
+      ky = pc.x;
+      kz = pc.y;
+      iyk = ky < 0 ? ky + N : ky;
+      const int kzc = kz < 0 ? 0 : kz;
+      cf_pen = invw[iyk] * invw[kzc] * (M == 2 ? 0.5f : 1.f);
+      ph_pen = cmul(phs[iyk], phs[kzc]);
+    }
+    float2* Tb = T0 + (s & 1) * N * P;
+    FftRunTo<N, 0, fft_nstages(N) - 1, true, false>::run(Tb, P, 1, P, tw);
+    float2 v[E];
+    fft_last_stage_regs<N, true, false>(Tb + p, P, tl, tw, v);
+    const int pw = (gi == 0) ? 0 : (gi <= 3 ? gi - 1 : gi - 4);  // power of k_x
+#pragma unroll
+    for (int q = 0; q < NBL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int e = q * RL + r;
+        const int kx = tl + q * TPL + r * (N / RL);
+        const int mx = kx <= N / 2 ? kx : kx - N;
+        float2 X = v[e];
+        if (M == 2 && mj == 1) X = cmul(X, cmul(phs[kx], ph_pen));
+        float kp = cf_pen * invw[kx];
+        for (int u = 0; u < pw; ++u) kp *= (float)mx;
+        if (gi == 0) {
+          if (mj == 0) a0[e] = make_float2(kp * X.x, kp * X.y);
+          else { a0[e].x = fmaf(kp, X.x, a0[e].x); a0[e].y = fmaf(kp, X.y, a0[e].y); }
+        } else if ((gi == 1 || gi == 4) && mj == 0) {
+          ga[e] = make_float2(kp * X.x, kp * X.y);
+        } else {
+          ga[e].x = fmaf(kp, X.x, ga[e].x);
+          ga[e].y = fmaf(kp, X.y, ga[e].y);
+        }
+      }
+    const bool complete = (mj == M - 1) && (gi == 0 || gi == 3 || gi == 8);
+    if (complete) {
+      const int slot = gi == 0 ? 0 : (gi == 3 ? 1 : 2);
+      float* wb = wbin + (warp * 3 + slot) * nbins;
+#pragma unroll
+      for (int q = 0; q < NBL; ++q)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int e = q * RL + r;
+          const int kx = tl + q * TPL + r * (N / RL);
+          const int mx = kx <= N / 2 ? kx : kx - N;
+          const int n2 = mx * mx + ky * ky + kz * kz;
+          const int bin = (kz >= 0 && n2 < n2_hi) ? lut[n2] : -1;
+          if (bin >= 0) {
+            const float wgt = kz == 0 ? 1.f : 2.f;
+            float val;
+            if (slot == 0) {
+              val = wgt * (a0[e].x * a0[e].x + a0[e].y * a0[e].y);
+            } else {
+              const float inv = 1.f / (float)n2;
+              val = wgt * (slot == 1 ? inv : inv * inv) * (a0[e].x * ga[e].x + a0[e].y * ga[e].y);
+            }
+            atomicAdd(wb + bin, val);
+          }
+        }
+    }
+    if (t == TILES - 1) {  // fold the float bins of this pencil block into FP64
+      __syncthreads();
+      for (int b = tid; b < 3 * nbins; b += blockDim.x) {
+        float sum = 0.f;
+        for (int w = 0; w < NW; ++w) {
+          sum += wbin[w * 3 * nbins + b];
+          wbin[w * 3 * nbins + b] = 0.f;
+        }
+        cbin[b] += (double)sum;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) {
+      atomicExch(err, 2);
+      // let any copy still in flight land before the CTA exits (bounded)
+      for (int b = 0; b < 2; ++b) mbar_wait(&bar[b], 0, 1LL << 20);
+    }
+    return;
+  }
+  for (int b = tid; b < 3 * nbins; b += blockDim.x)
+    if (cbin[b] != 0.0) atomicAdd(&acc[b], cbin[b]);
 }
 
 }  // namespace ys

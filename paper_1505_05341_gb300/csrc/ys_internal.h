@@ -1,5 +1,6 @@
 // Internal plan state and kernel entry points of the ystat library.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -18,7 +19,7 @@ enum SumSlot {
   SUM_WR2 = 3,   // sum_ran w^2
   SUM_WR2N = 4,  // sum_ran w^2 nbar
   SUM_BAD = 5,   // particles outside the box
-  SUM_HAS_NBAR = 6,
+  SUM_TIMEOUT = 6,   // set when a bounded device-side wait ran out
   SUM_COUNT = 8
 };
 
@@ -43,7 +44,10 @@ struct Plan {
   int ntiles = 0;
   // pencils (k_y, k_z) kept for the x transform: k_y^2 + k_z^2 < n2_hi
   int n2_hi = 0, nzc = 0, np = 0;
-  int batch = 1;                 // planes per y,z-transform batch
+  int np_pad = 0;                // np rounded up to whole x-stage pencil blocks
+  int ring_slots = 1;            // S: planes held by the y,z-stage ring
+  int ring_lead = 1;             // D: column items trail row items by D planes
+  int yz_grid = 1;               // CTAs of the persistent y,z kernel
   // device tables
   float2* d_tw = nullptr;        // [n] exp(-2 pi i j / n)
   float2* d_nodes = nullptr;     // [3][n + 3] node positions (hi, lo), index offset 1
@@ -56,8 +60,10 @@ struct Plan {
   double* d_shell = nullptr;     // [2][n_bins] mode count and sum |k| (host-built)
   // buffers
   float* d_mesh = nullptr;       // [m][n][n][n]
-  float2* d_z = nullptr;         // [nb][batch][nzc][n] y,z-stage scratch
-  float2* d_g = nullptr;         // [m][ng][n][np] grouped y,z transforms
+  float2* d_z = nullptr;         // [S][nb][nzc][n] y,z-stage ring of z-transformed planes
+  int* d_sync = nullptr;         // [2 m n + 2] per-plane counters, ticket, error flag
+  float2* d_g = nullptr;         // [m][ng][n][np_pad] grouped y,z transforms
+  CUtensorMap gmap;              // 2D tensor map of d_g for the x-stage TMA loads
   double* d_acc = nullptr;       // [3][n_bins] shell sums
   double* d_sums = nullptr;      // [SUM_COUNT]
   double* d_result = nullptr;    // [5 n_bins + 3]

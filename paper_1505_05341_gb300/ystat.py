@@ -66,7 +66,7 @@ class YsResult(ctypes.Structure):
 
 
 NUM_KERNEL_CLASSES = 8
-KERNEL_CLASSES = ["particle_count", "tile_scan", "particle_bin", "tile_deposit", "yz_rows", "yz_cols",
+KERNEL_CLASSES = ["particle_count", "tile_scan", "particle_bin", "tile_deposit", "yz_stage", "unused",
                   "x_combine", "finalize"]
 
 
