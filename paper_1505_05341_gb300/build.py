@@ -44,7 +44,8 @@ def _gen_table():
 
 
 def _compile(nvcc, src, obj, verbose):
-    cmd = [nvcc, *FLAGS, *ARCH, "-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
+    extra = os.environ.get("YS_NVCC_FLAGS", "").split()
+    cmd = [nvcc, *FLAGS, *extra, *ARCH, "-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

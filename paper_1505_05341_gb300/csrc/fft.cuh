@@ -14,15 +14,24 @@ namespace ys {
 
 __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
-// Elements per thread: chosen so that one line is handled by at most one warp
-// (N / E <= 32) up to N = 512 (and 768), which lets the stages synchronise with
-// __syncwarp instead of a block-wide barrier.
+// Elements per thread.  Walked by consecutive threads (y,z stage), a line fits one
+// warp up to N = 512 (768); its TPL = N / E threads synchronise among themselves only
+// (line_group_sync).  Interleaved lines (x stage) use 8 or 12 elements.
 __host__ __device__ constexpr int fft_elems(int n) {
-  return is_pow2(n) ? (n >= 512 ? 16 : 8) : (n >= 768 ? 24 : 12);
+  return is_pow2(n) ? 8 : 12;
 }
-
-// Elements per thread for layouts whose lines interleave (x-stage): 8 or 12.
 __host__ __device__ constexpr int fft_elems_lf(int n) { return is_pow2(n) ? 8 : 12; }
+
+// Barrier over the TPL consecutive threads that own one line: the warp when the
+// line fits in it, else a named barrier (ids 1..15) shared by those threads only.
+template <int TPL>
+__device__ __forceinline__ void line_group_sync() {
+  if constexpr (TPL <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / TPL)), "r"(TPL) : "memory");
+  }
+}
 
 // Number of stages and the radix of stage s (see header comment).
 __host__ __device__ constexpr int fft_nstages(int n) {
@@ -134,8 +143,11 @@ __host__ __device__ constexpr int fft_line_len() { return PAD ? N + N / 8 + 1 : 
 // One Stockham stage over `nl` lines of length N stored in shared memory at
 // buf[line * ls + elem * es].  LF: consecutive threads take consecutive lines (for
 // layouts whose lines interleave); otherwise consecutive threads walk one line.
-template <int N, int S, bool LF, bool PAD>
-__device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, const float2* tw) {
+// NL > 0: the number of lines is a compile-time constant (passes unrolled, separated
+// by a line-group barrier so that no pass's addresses are hoisted into another);
+// NL == 0: nl lines at run time.
+template <int N, int S, bool LF, bool PAD, int NL = 0>
+__device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt, const float2* tw) {
   constexpr int R = fft_radix(N, S);
   constexpr int E = LF ? fft_elems_lf(N) : fft_elems(N);
   constexpr int TPL = N / E;        // threads per line
@@ -143,13 +155,14 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, c
   constexpr int NS = fft_ns_before(N, S);
   constexpr int STRIDE = N / R;
   constexpr int TWS = N / (NS * R);
-  // A line lives inside one warp when it is walked by consecutive threads and TPL <= 32.
-  constexpr bool WARP_LOCAL = !LF && TPL <= 32;
+  // Lines walked by consecutive threads only need their own threads synchronised.
   const int tid = threadIdx.x;
   const int lpp = blockDim.x / TPL;  // lines per pass
   const bool in_pass = tid < lpp * TPL;
   const int lane_line = LF ? tid % lpp : tid / TPL;
   const int tl = LF ? tid / lpp : tid % TPL;
+  const int nl = NL > 0 ? NL : nl_rt;
+#pragma unroll 1
   for (int base_line = 0; base_line < nl; base_line += lpp) {
     const int line = base_line + lane_line;
     const bool ok = in_pass && line < nl;
@@ -163,7 +176,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, c
         for (int r = 0; r < R; ++r) v[q * R + r] = lp[fft_pos<PAD>(j + r * STRIDE) * es];
       }
     }
-    if (WARP_LOCAL) __syncwarp(); else __syncthreads();
+    if constexpr (LF) __syncthreads(); else line_group_sync<TPL>();
     if (ok) {
       float2* lp = buf + (size_t)line * ls;
 #pragma unroll
@@ -180,20 +193,20 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl, c
         for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(outb + r * NS) * es] = v[q * R + r];
       }
     }
-    if (WARP_LOCAL) __syncwarp(); else __syncthreads();
+    if constexpr (LF) __syncthreads(); else line_group_sync<TPL>();
   }
 }
 
 // Terminate the recursion at S == number of stages.
-template <int N, int S, bool LF, bool PAD = false, bool Done = (S >= fft_nstages(N))>
+template <int N, int S, bool LF, bool PAD = false, int NL = 0, bool Done = (S >= fft_nstages(N))>
 struct FftRun {
   __device__ static __forceinline__ void run(float2* buf, int es, int ls, int nl, const float2* tw) {
-    fft_stage<N, S, LF, PAD>(buf, es, ls, nl, tw);
-    FftRun<N, S + 1, LF, PAD>::run(buf, es, ls, nl, tw);
+    fft_stage<N, S, LF, PAD, NL>(buf, es, ls, nl, tw);
+    FftRun<N, S + 1, LF, PAD, NL>::run(buf, es, ls, nl, tw);
   }
 };
-template <int N, int S, bool LF, bool PAD>
-struct FftRun<N, S, LF, PAD, true> {
+template <int N, int S, bool LF, bool PAD, int NL>
+struct FftRun<N, S, LF, PAD, NL, true> {
   __device__ static __forceinline__ void run(float2*, int, int, int, const float2*) {}
 };
 
@@ -266,8 +279,8 @@ struct FftRunTo<N, S, END, LF, PAD, true> {
 };
 
 // In-place forward FFT of nl lines held in shared memory.  Every thread of the block
-// must call it.  blockDim.x must be >= N / E.  When a line is local to one warp the
-// stages only synchronise the warp: callers reading other warps' lines afterwards
+// must call it.  blockDim.x must be >= N / E.  Unless LF, the stages only
+// synchronise the threads of each line: callers reading other lines afterwards
 // need a __syncthreads() first.
 template <int N, bool LF, bool PAD = false>
 __device__ __forceinline__ void fft_smem(float2* buf, int es, int ls, int nl, const float2* tw) {

@@ -92,20 +92,19 @@ def emit(ell_max):
     lines.append(f"template <> struct GroupTable<{ell_max}> {{")
     lines.append(f"  static constexpr int NB = {nb};")
     lines.append(f"  static constexpr int NG = {ng};")
-    lines.append("  // G_g(k_y, k_z) = sum_beta poly_{g,beta}(k_y, k_z) Psi_beta; psi(beta) reads Psi_beta.")
-    lines.append("  template <class PsiAt>")
-    lines.append("  __device__ static __forceinline__ void combine(PsiAt psi, float ky, float kz, float2 (&g)[NG]) {")
+    lines.append("  // G_g(k_y, k_z) += sum_{LO <= beta < HI} poly_{g,beta}(k_y, k_z) Psi_beta, where psi(beta)")
+    lines.append("  // returns Psi_beta; combine() zeroes G and adds every basis field.")
+    lines.append("  template <int LO, int HI, class PsiAt>")
+    lines.append("  __device__ static __forceinline__ void accumulate(PsiAt psi, float ky, float kz, float2 (&g)[NG]) {")
     lines.append("    float kyp[5], kzp[5];")
     lines.append("    kyp[0] = 1.f; kzp[0] = 1.f;")
     lines.append("    #pragma unroll")
     lines.append("    for (int i = 1; i < 5; ++i) { kyp[i] = kyp[i - 1] * ky; kzp[i] = kzp[i - 1] * kz; }")
-    for gi in range(ng):
-        lines.append(f"    g[{gi}] = make_float2(0.f, 0.f);")
     by_beta = {}
     for (gi, beta), poly in sorted(tab.items()):
         by_beta.setdefault(beta, []).append((gi, poly))
     for beta in sorted(by_beta):
-        lines.append(f"    {{ const float2 ps = psi({beta});")
+        lines.append(f"    if constexpr (LO <= {beta} && {beta} < HI) {{ const float2 ps = psi({beta});")
         for gi, poly in by_beta[beta]:
             terms = []
             for (b, c), v in sorted(poly.items()):
@@ -114,6 +113,12 @@ def emit(ell_max):
             lines.append(f"      {{ const float w = {' + '.join(terms)};")
             lines.append(f"        g[{gi}].x = fmaf(w, ps.x, g[{gi}].x); g[{gi}].y = fmaf(w, ps.y, g[{gi}].y); }}")
         lines.append("    }")
+    lines.append("  }")
+    lines.append("  template <class PsiAt>")
+    lines.append("  __device__ static __forceinline__ void combine(PsiAt psi, float ky, float kz, float2 (&g)[NG]) {")
+    for gi in range(ng):
+        lines.append(f"    g[{gi}] = make_float2(0.f, 0.f);")
+    lines.append(f"    accumulate<0, {nb}>(psi, ky, kz, g);")
     lines.append("  }")
     arr = ", ".join(f"{a}, {b}, {c}, {d}" for a, b, c, d in bs)
     lines.append("  // mono_c(beta, i): i = 0, 1, 2 exponents of r_hat_x, r_hat_y, r_hat_z; i = 3 degree.")

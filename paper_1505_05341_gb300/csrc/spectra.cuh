@@ -40,6 +40,27 @@ __device__ __forceinline__ float ipow(float v) {
   return r;
 }
 
+// Value at one node of a basis field given by its exponents (a, b, c) and degree d
+// (uniform across the warp): d = 0 -> F, d = -1 -> F without the r = 0 node,
+// d = -2 -> none (0), else F r_hat_x^a r_hat_y^b r_hat_z^c with a, b <= 4, c <= 1.
+__device__ __forceinline__ float basis_value_rt(float f, float xh, float yh, float zh, bool nonzero_r, int a, int b,
+                                                int c, int d) {
+  if (d == 0) return f;
+  if (d == -1) return nonzero_r ? f : 0.f;
+  if (d == -2) return 0.f;
+  float v = f;
+  if (a >= 1) v *= xh;
+  if (a >= 2) v *= xh;
+  if (a >= 3) v *= xh;
+  if (a >= 4) v *= xh;
+  if (b >= 1) v *= yh;
+  if (b >= 2) v *= yh;
+  if (b >= 3) v *= yh;
+  if (b >= 4) v *= yh;
+  if (c >= 1) v *= zh;
+  return v;
+}
+
 // Value of basis field BETA at one node (compile-time exponents; 0 past the last field).
 template <int ELL, int BETA>
 __device__ __forceinline__ float basis_value(float f, float xh, float yh, float zh, bool nonzero_r) {
@@ -118,11 +139,6 @@ __device__ __forceinline__ bool wait_geq(const int* addr, int target, int* err, 
   return true;
 }
 
-__device__ __forceinline__ void signal_done(int* counter) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(counter, 1);
-}
 
 template <int N, int ELL>
 struct YZ {
@@ -148,79 +164,78 @@ __device__ __forceinline__ void line_sync() {
   if constexpr (N / fft_elems(N) <= 32) __syncwarp(); else __syncthreads();
 }
 
-// One pair of basis fields for the R rows of a row item: fields at the nodes (first
-// FFT stage from registers), FFT along z, then the split of the two real fields into
-// their half spectra, written to the ring slot.  C is one of two line buffers, so
-// the split of this pair can overlap the FFT of the next.
-template <int N, int ELL, int PAIR>
-__device__ __noinline__ void row_pair(float2* C, const float* __restrict__ plane, float X,
+// One pair of basis fields (fa = 2 pr, fb = 2 pr + 1) for the R rows of a row item:
+// fields at the nodes (first FFT stage from registers, one butterfly at a time),
+// FFT along z, then the split of the two real fields into their half spectra,
+// written to the ring slot.  C is one of two line buffers, so the split of this pair
+// can overlap the FFT of the next.
+template <int N, int ELL>
+__device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restrict__ plane, float X,
                                          const float* __restrict__ rely, const float* __restrict__ relz, int row0,
                                          const float2* tw, float2* __restrict__ zslot, int nzc) {
   using Y = YZ<N, ELL>;
   constexpr int E = Y::E, TPL = Y::TPL, R0 = Y::R0, R = Y::R, NB = Y::NB, LL = Y::LL, LPP = Y::LPP;
+  const int fa = 2 * pr, fb = 2 * pr + 1;
+  int aa, ab, ac, ad, ba, bb, bc, bd;
+  GroupTable<ELL>::mono(fa, aa, ab, ac, ad);
+  GroupTable<ELL>::mono(fb, ba, bb, bc, bd);
   const int tl = threadIdx.x % TPL;
 #pragma unroll
   for (int ps = 0; ps < Y::PASSES; ++ps) {
     const int row = ps * LPP + threadIdx.x / TPL;
     if (row < R) {
       const float Yc = rely[row0 + row];
-      float2 v[E];
-#pragma unroll
-      for (int q = 0; q < E / R0; ++q)
+      const float* frow = plane + (size_t)(row0 + row) * N;
+      float2* lp = C + row * LL;
+#pragma unroll 1
+      for (int q = 0; q < E / R0; ++q) {
+        float2 v[R0];
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int z = fft_in_index<N>(tl, q, r);
           const float Zc = relz[z];
-          const float f = plane[(size_t)(row0 + row) * N + z];
+          const float f = frow[z];
           const float r2 = fmaf(X, X, fmaf(Yc, Yc, Zc * Zc));
           const bool nz = r2 > 0.f;
           const float rinv = nz ? rsqrtf(r2) : 0.f;
           const float xh = X * rinv, yh = Yc * rinv, zh = Zc * rinv;
-          v[q * R0 + r] = make_float2(basis_value<ELL, 2 * PAIR>(f, xh, yh, zh, nz),
-                                      basis_value<ELL, 2 * PAIR + 1>(f, xh, yh, zh, nz));
+          v[r] = make_float2(basis_value_rt(f, xh, yh, zh, nz, aa, ab, ac, ad),
+                             basis_value_rt(f, xh, yh, zh, nz, ba, bb, bc, bd));
         }
-      fft_stage0_regs<N, true>(v, C + row * LL, 1, tl);
+        Dft<R0>::run(v);
+        const int jq = tl + q * TPL;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) lp[fft_pos<true>(jq * R0 + r)] = v[r];
+      }
     }
   }
   line_sync<N>();
-  FftRun<N, 1, false, true>::run(C, 1, LL, R, tw);
+  FftRun<N, 1, false, true, R>::run(C, 1, LL, R, tw);
   __syncthreads();
-  constexpr int FA = 2 * PAIR, FB = 2 * PAIR + 1;
   for (int e = threadIdx.x; e < nzc * R; e += blockDim.x) {
     const int kz = e / R, r = e - kz * R;
     const float2 ck = C[r * LL + fft_pos<true>(kz)];
     const float2 cm = C[r * LL + fft_pos<true>(kz == 0 ? 0 : N - kz)];
     // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i).
-    zslot[((size_t)FA * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
-    if constexpr (FB < NB)
-      zslot[((size_t)FB * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
+    zslot[((size_t)fa * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
+    if (fb < NB)
+      zslot[((size_t)fb * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
   }
 }
 
 template <int N, int ELL>
-__device__ __noinline__ void row_item(float2* work, const float* __restrict__ plane, float X,
+__device__ __forceinline__ void row_item(float2* work, const float* __restrict__ plane, float X,
                                          const float* __restrict__ rely, const float* __restrict__ relz, int row0,
                                          const float2* tw, float2* __restrict__ zslot, int nzc) {
   using Y = YZ<N, ELL>;
-  constexpr int E = Y::E, TPL = Y::TPL, R0 = Y::R0, R = Y::R, LL = Y::LL, LPP = Y::LPP;
+  constexpr int R = Y::R, LL = Y::LL;
 #pragma unroll 1
-  for (int pr = 0; pr < Y::NPAIR; ++pr) {
-    float2* C = work + (pr & 1) * R * LL;
-    switch (pr) {
-      case 0: row_pair<N, ELL, 0>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      case 1: row_pair<N, ELL, 1>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      case 2: row_pair<N, ELL, 2>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      case 3: row_pair<N, ELL, 3>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      case 4: row_pair<N, ELL, 4>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      case 5: row_pair<N, ELL, 5>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      case 6: row_pair<N, ELL, 6>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-      default: row_pair<N, ELL, 7>(C, plane, X, rely, relz, row0, tw, zslot, nzc); break;
-    }
-  }
+  for (int pr = 0; pr < Y::NPAIR; ++pr)
+    row_pair<N, ELL>(pr, work + (pr & 1) * R * LL, plane, X, rely, relz, row0, tw, zslot, nzc);
 }
 
 template <int N, int ELL>
-__device__ __noinline__ void column_fold(const float2* S, int kz, const int* __restrict__ col_off,
+__device__ __forceinline__ void column_fold(const float2* S, int kz, const int* __restrict__ col_off,
                                          float2* __restrict__ gout, int j, int ix, int np) {
   using Y = YZ<N, ELL>;
   constexpr int NG = Y::NG, LL = Y::LL;
@@ -238,7 +253,7 @@ __device__ __noinline__ void column_fold(const float2* S, int kz, const int* __r
 }
 
 template <int N, int ELL>
-__device__ __noinline__ void column_item(float2* S, const float2* __restrict__ zs, int nzc, int kz,
+__device__ __forceinline__ void column_item(float2* S, const float2* __restrict__ zs, int nzc, int kz,
                                             const int* __restrict__ col_off, const float2* tw,
                                             float2* __restrict__ gout, int j, int ix, int np) {
   using Y = YZ<N, ELL>;
@@ -257,13 +272,25 @@ __device__ __noinline__ void column_item(float2* S, const float2* __restrict__ z
     }
   }
   line_sync<N>();
-  FftRun<N, 1, false, true>::run(S, 1, LL, NB, tw);
+  FftRun<N, 1, false, true, NB>::run(S, 1, LL, NB, tw);
   __syncthreads();
   column_fold<N, ELL>(S, kz, col_off, gout, j, ix, np);
 }
 
+// Completion of one item: every thread's writes are ordered before thread 0's
+// release-add by the barrier (the release is cumulative over them).
+__device__ __forceinline__ void signal_release(int* counter) {
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(counter) : "memory");
+}
+
+// Resident CTAs per SM the y,z kernel is compiled for (register budget 65536 / (256 x this)).
+#ifndef YS_YZ_MIN_BLOCKS
+#define YS_YZ_MIN_BLOCKS 2
+#endif
+
 template <int N, int ELL>
-__global__ void __launch_bounds__(256, (N >= 1024 ? 1 : 2)) k_yz(YZParams prm) {
+__global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(YZParams prm) {
   using Y = YZ<N, ELL>;
   constexpr int R = Y::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -279,6 +306,8 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : 2)) k_yz(YZParams prm) {
   const size_t slot_elems = (size_t)Y::NB * prm.nzc * N;
   __syncthreads();
   for (;;) {
+    // One ticket at a time: a claimed item must start at once, since later items
+    // may depend on it.
     if (threadIdx.x == 0) s_item = atomicAdd(prm.ticket, 1);
     __syncthreads();
     const int item = s_item;
@@ -295,7 +324,7 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : 2)) k_yz(YZParams prm) {
         const float* rel = prm.rel + (size_t)j * 3 * N;
         row_item<N, ELL>(work, prm.mesh + j * n3 + (size_t)ix * N * N, rel[ix], rel + N, rel + 2 * N, sub * R, tw,
                          prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc);
-        signal_done(prm.done_z + p);
+        signal_release(prm.done_z + p);
       }
     } else {
       const int p = step - prm.D;  // column item of plane p
@@ -306,10 +335,10 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : 2)) k_yz(YZParams prm) {
         const int j = p / N, ix = p - j * N;
         column_item<N, ELL>(work, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc, sub - NZ, prm.col_off, tw,
                             prm.gout, j, ix, prm.np);
-        signal_done(prm.done_y + p);
+        signal_release(prm.done_y + p);
       }
     }
-    __syncthreads();
+    __syncthreads();  // s_item is rewritten at the top of the next round
   }
 }
 

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ystat.h"
+#include "ystat.h"  // include/ (on the -I path)
 
 namespace ys {
 
