@@ -329,6 +329,11 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "p0_first_bins": [float(v) for v in res.p0[:3]],
     }
+    if world == 1 and not args.no_batched and args.workload == WORKLOAD:
+        del dgal, dran
+        plan.close()
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(max(1, min(args.steps, 3)), 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_cat, sample, cores = cpu_sample(gal, ran, geo)
         line["cpu_baseline"] = {"value": 1.0 / per_cat, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -338,6 +343,86 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_catalogues(n_cat=256, first_seed=1000):
+    """The batched-mock workload on the GPU: per catalogue (seed, n_gal, mesh) from
+    synth.batched_cube_specs; uniform points in the 500 Mpc/h cube centred on
+    (600, 600, 600), observer at the origin, unit weights, nbar = n_gal / 500^3; the
+    points are drawn on the device from a generator seeded with the catalogue seed."""
+    import torch
+    import synth
+    specs = synth.batched_cube_specs(n_cat, first_seed)
+    lo, side = 350.0, 500.0
+    gals, rans = [], []
+    for seed, ng, nr, mesh in specs:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed)
+        nbar = ng / side ** 3
+        cats = []
+        for n in (ng, nr):
+            p = lo + side * torch.rand((3, n), generator=gen, device="cuda", dtype=torch.float64)
+            p = p.to(torch.float32).clamp_(max=float(np.nextafter(np.float32(lo + side), np.float32(0))))
+            cats.append((p[0].contiguous(), p[1].contiguous(), p[2].contiguous(),
+                         torch.ones(n, device="cuda"), torch.full((n,), nbar, device="cuda")))
+        gals.append(cats[0])
+        rans.append(cats[1])
+    return specs, gals, rans
+
+
+def run_batched(steps, warmup):
+    """Batched-mock throughput: one graph launch over all catalogues, against the same
+    catalogues run one at a time through the plain path (one plan per mesh size)."""
+    import torch
+    import paper_1505_05341_gb300 as ys
+    specs, gals, rans = batched_catalogues()
+    cfgs = [ys.make_config(mesh, (350.0,) * 3, 500.0, (0.0, 0.0, 0.0), assign="cic", interlace=False, dk=0.01,
+                           max_particles=ng + nr) for seed, ng, nr, mesh in specs]
+    batch = ys.Batch(cfgs, branches=4)
+    out = torch.zeros((batch.n, batch.stride), dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    batch.autotune(gals, rans, reps=2)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, warmup)):
+        batch.run(gals, rans, out, stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        batch.run(gals, rans, out, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / steps
+    rows = batch.results(out)
+    bad = sum(1 for r in rows if r.status != 0)
+    batch.close()
+    # plain path: one plan per mesh size, catalogues one after another
+    plans = {}
+    for (seed, ng, nr, mesh) in specs:
+        if mesh not in plans:
+            cap = max(g + r for s_, g, r, m in specs if m == mesh)
+            plans[mesh] = ys.Plan(mesh, (350.0,) * 3, 500.0, (0.0, 0.0, 0.0), assign="cic", dk=0.01,
+                                  max_particles=cap, stream=stream.cuda_stream)
+    def plain_pass():
+        for i, (seed, ng, nr, mesh) in enumerate(specs):
+            plans[mesh].assign(gals[i], rans[i])
+            plans[mesh].measure_async(out[i])
+    plain_pass()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    for pl in plans.values():
+        pl.close()
+    meshes = {m: sum(1 for s_ in specs if s_[3] == m) for m in (128, 192, 256)}
+    return {"value": len(specs) / (ms_batch / 1e3), "unit": UNIT, "n_catalogs": len(specs),
+            "ms_per_batch": ms_batch, "plain_value": len(specs) / (ms_plain / 1e3),
+            "speedup_vs_plain": ms_plain / ms_batch, "meshes": meshes, "assign": "cic", "branches": 4,
+            "autotune_s": tune_s, "rows_with_errors": bad,
+            "particles": int(sum(g + r for s_, g, r, m in specs))}
 
 
 def plan_pencils(plan):
@@ -369,6 +454,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -194,6 +194,52 @@ ys_status ys_assign_noalloc(ys_plan* plan, const ys_catalog* gal, const ys_catal
 /* Free everything the plan owns.  NULL is accepted. */
 ys_status ys_plan_destroy(ys_plan* plan);
 
+/* ---- Autotuning and batched runs (throughput arrangements; no counterpart in the
+ * paper's equations, which these calls evaluate unchanged) ---- */
+
+/* Launch shapes the autotuner chose: scatter tile (nodes per axis) and CTAs of the
+ * persistent y,z kernel, with the best measured times. */
+typedef struct {
+  int32_t tile[3];
+  int32_t yz_grid;
+  double assign_ms;
+  double measure_ms;
+} ys_tuning;
+
+/* Time the candidate scatter tiles (16x16x32, 8x16x32, 16x16x16, 32x16x32, 8x8x32)
+ * and y,z grids (resident, 3/4, 1/2) on this catalogue (DEVICE pointers), reps timed
+ * calls each, and keep the fastest in the plan.  Leaves the catalogue assigned.
+ * Synchronous.  out may be NULL. */
+ys_status ys_plan_autotune(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran, int32_t reps,
+                           ys_tuning* out);
+
+typedef struct ys_batch_s ys_batch;
+
+/* Many catalogues -- the Sec. 1 use case of hundreds of mocks -- in one graph launch.
+ * cfgs[i] configures catalogue i (its max_particles must bound gal_i.n + ran_i.n; its
+ * stream is ignored).  Catalogues are spread over `branches` concurrent streams
+ * (1..32); each (branch, configuration) pair gets its own plan.  Host-side. */
+ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys_batch** out);
+
+/* Doubles between consecutive result rows of ys_batch_run: 5 n_bins_max + 5. */
+int64_t ys_batch_result_stride(const ys_batch* batch);
+
+/* Autotune every plan of the batch on its largest catalogue (DEVICE pointers,
+ * arrays of n).  Synchronous. */
+ys_status ys_batch_autotune(ys_batch* batch, const ys_catalog* gal, const ys_catalog* ran, int32_t reps);
+
+/* Run the whole batch.  gal, ran: host arrays of n catalogues holding DEVICE pointers.
+ * Row i of d_results (DEVICE, n x stride doubles) receives catalogue i's result row in
+ * the layout of ys_measure_multipoles_async.  The first call, and any call whose
+ * catalogue pointers, sizes or d_results differ from the last capture, captures the
+ * batch into a CUDA graph (host-side work); later calls only launch it on `stream`
+ * (cudaStream_t, NULL = legacy stream).  Asynchronous otherwise. */
+ys_status ys_batch_run(ys_batch* batch, const ys_catalog* gal, const ys_catalog* ran, double* d_results,
+                       void* stream);
+
+/* Free the batch and its plans.  NULL is accepted. */
+ys_status ys_batch_destroy(ys_batch* batch);
+
 /* Static description of a status code. */
 const char* ys_status_string(ys_status s);
 

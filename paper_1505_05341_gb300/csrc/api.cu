@@ -17,9 +17,10 @@ template <int N> cudaError_t run_measure_n(Plan& p);
 template <int N> int yz_grid_n(int ell, cudaError_t* err);
 template <int N> int x_pencils_n();
 
-namespace {
-
 thread_local std::string g_last_cuda_error;
+int yz_row_items(int n);
+
+namespace {
 
 ys_status cuda_fail(cudaError_t e) {
   g_last_cuda_error = cudaGetErrorString(e);
@@ -242,6 +243,14 @@ ys_status build_tables(Plan& p) {
   return YS_OK;
 }
 
+bool catalog_ok(const ys_catalog* k) {
+  if (!k || k->n < 0) return false;
+  if (k->n > 0 && (!k->x || !k->y || !k->z)) return false;
+  return true;
+}
+
+}  // namespace
+
 ys_status ensure_particles(Plan& p, int64_t total) {
   if (total <= p.part_cap) return YS_OK;
   cudaError_t e;
@@ -251,8 +260,14 @@ ys_status ensure_particles(Plan& p, int64_t total) {
     dfree(p.d_rec);
     dfree(p.d_rec_cell);
   }
+  // records per particle: up to 2 tiles per axis that has more than one tile, for
+  // any scatter-tile shape the tuner may switch to
   int factor = 1;
-  for (int a = 0; a < 3; ++a) factor *= p.geom.tiles[a] > 1 ? 2 : 1;
+  for (const auto& t : kTileCandidates) {
+    int f = 1;
+    for (int a = 0; a < 3; ++a) f *= std::min(t[a], p.n) < p.n ? 2 : 1;
+    factor = std::max(factor, f);
+  }
   p.part_cap = total;
   p.rec_cap = total * factor;
   if ((e = dalloc(p, p.d_rec, (size_t)p.rec_cap))) return cuda_fail(e);
@@ -260,13 +275,22 @@ ys_status ensure_particles(Plan& p, int64_t total) {
   return YS_OK;
 }
 
-bool catalog_ok(const ys_catalog* k) {
-  if (!k || k->n < 0) return false;
-  if (k->n > 0 && (!k->x || !k->y || !k->z)) return false;
-  return true;
+void set_tiles(Plan& p, int tx, int ty, int tz) {
+  const int t[3] = {tx, ty, tz};
+  p.ntiles = 1;
+  for (int a = 0; a < 3; ++a) {
+    p.geom.tdim[a] = std::min(t[a], p.n);
+    p.geom.tiles[a] = p.n / p.geom.tdim[a];
+    p.ntiles *= p.geom.tiles[a];
+  }
 }
 
-}  // namespace
+void set_yz_grid(Plan& p, int grid) {
+  p.yz_grid = std::max(1, std::min(grid, p.yz_grid_max));
+  const int items_per_plane = yz_row_items(p.n) + std::max(1, p.nzc);
+  p.ring_lead = (p.yz_grid + items_per_plane - 1) / items_per_plane + 1;
+  p.ring_slots = std::min(p.m * p.n, p.ring_lead + 2);
+}
 
 LaunchScope::LaunchScope(Plan& plan, int c) : p(plan), cls(c) {
   if (p.capturing) {
@@ -400,14 +424,14 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   ys::Geom& g = p.geom;
   g.n = n;
   g.inv_h = (float)(n / c.box_len);
-  const int tdef[3] = {ys::TILE_X, ys::TILE_Y, ys::TILE_Z};
-  p.ntiles = 1;
-  for (int a = 0; a < 3; ++a) {
-    g.bmin[a] = (float)c.box_min[a];
-    g.tdim[a] = std::min(tdef[a], n);
-    g.tiles[a] = n / g.tdim[a];
-    p.ntiles *= g.tiles[a];
+  for (int a = 0; a < 3; ++a) g.bmin[a] = (float)c.box_min[a];
+  // tile counters sized for every scatter-tile candidate the tuner may pick
+  p.ntiles_max = 0;
+  for (const auto& t : ys::kTileCandidates) {
+    ys::set_tiles(p, t[0], t[1], t[2]);
+    p.ntiles_max = std::max(p.ntiles_max, p.ntiles);
   }
+  ys::set_tiles(p, ys::TILE_X, ys::TILE_Y, ys::TILE_Z);
   ys_status st = ys::build_tables(p);
   if (st != YS_OK) {
     ys::free_all(p);
@@ -417,24 +441,23 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   const size_t n3 = (size_t)n * n * n;
   // y,z-stage ring: the column items of a plane trail its row items by D planes, and a
   // slot is rewritten S = D + 2 planes later; D covers one grid's worth of items.
-  p.yz_grid = ys::yz_grid_for(p, &e);
+  p.yz_grid_max = ys::yz_grid_for(p, &e);
   if (e) {
     st = ys::cuda_fail(e);
     ys::free_all(p);
     delete h;
     return st;
   }
-  const int items_per_plane = ys::yz_row_items(p.n) + std::max(1, p.nzc);
-  p.ring_lead = (p.yz_grid + items_per_plane - 1) / items_per_plane + 1;
-  p.ring_slots = std::min(p.m * n, p.ring_lead + 2);
+  ys::set_yz_grid(p, p.yz_grid_max);  // ring sized for the largest grid
   const size_t slot = (size_t)p.nb * std::max(1, p.nzc) * n;
   if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, slot * p.ring_slots)) ||
       (e = ys::dalloc(p, p.d_sync, (size_t)2 * p.m * n + 2)) ||
       (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np_pad))) ||
       (e = ys::dalloc(p, p.d_acc, (size_t)3 * c.n_bins)) || (e = ys::dalloc(p, p.d_sums, (size_t)ys::SUM_COUNT)) ||
       (e = ys::dalloc(p, p.d_result, (size_t)5 * c.n_bins + 5)) ||
-      (e = ys::dalloc(p, p.d_tile_count, (size_t)p.ntiles)) || (e = ys::dalloc(p, p.d_tile_off, (size_t)p.ntiles + 1)) ||
-      (e = ys::dalloc(p, p.d_tile_cur, (size_t)p.ntiles))) {
+      (e = ys::dalloc(p, p.d_tile_count, (size_t)p.ntiles_max)) ||
+      (e = ys::dalloc(p, p.d_tile_off, (size_t)p.ntiles_max + 1)) ||
+      (e = ys::dalloc(p, p.d_tile_cur, (size_t)p.ntiles_max))) {
     st = ys::cuda_fail(e);
     ys::free_all(p);
     delete h;

@@ -23,8 +23,11 @@ enum SumSlot {
   SUM_COUNT = 8
 };
 
-// Tile of the scatter: TX x TY x TZ mesh nodes per CTA (capped at N per axis).
+// Tile of the scatter: TX x TY x TZ mesh nodes per CTA (capped at N per axis); the
+// default and the shapes the autotuner tries (each divides every supported N once
+// capped; shared memory = meshes x nodes x 4 bytes).
 constexpr int TILE_X = 16, TILE_Y = 16, TILE_Z = 32;
+constexpr int kTileCandidates[5][3] = {{16, 16, 32}, {8, 16, 32}, {16, 16, 16}, {32, 16, 32}, {8, 8, 32}};
 
 struct Geom {
   int n;            // mesh side N
@@ -48,6 +51,8 @@ struct Plan {
   int ring_slots = 1;            // S: planes held by the y,z-stage ring
   int ring_lead = 1;             // D: column items trail row items by D planes
   int yz_grid = 1;               // CTAs of the persistent y,z kernel
+  int yz_grid_max = 1;           // resident CTAs of that kernel (upper bound for tuning)
+  int ntiles_max = 0;            // tile-counter capacity over the scatter tile candidates
   // device tables
   float2* d_tw = nullptr;        // [n] exp(-2 pi i j / n)
   float2* d_nodes = nullptr;     // [3][n + 3] node positions (hi, lo), index offset 1
@@ -105,6 +110,12 @@ struct LaunchScope {
 
 // Kernel launchers (return cudaError_t of the launch).
 cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran);
+// Scatter tile shape (nodes per axis, capped at N); updates geom and ntiles.
+void set_tiles(Plan& p, int tx, int ty, int tz);
+// y,z grid size; updates the ring lead D and slots S (S never exceeds the allocation).
+void set_yz_grid(Plan& p, int grid);
+ys_status ensure_particles(Plan& p, int64_t total);
+extern thread_local std::string g_last_cuda_error;
 cudaError_t launch_measure(Plan& p);
 ys_status assign_noalloc(Plan& p, const ys_catalog& gal, const ys_catalog& ran, std::string& why);
 

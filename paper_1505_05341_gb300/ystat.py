@@ -74,6 +74,11 @@ class YsStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * NUM_KERNEL_CLASSES), ("ms", ctypes.c_double * NUM_KERNEL_CLASSES)]
 
 
+class YsTuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32 * 3), ("yz_grid", ctypes.c_int32), ("assign_ms", ctypes.c_double),
+                ("measure_ms", ctypes.c_double)]
+
+
 class YstatError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -106,12 +111,22 @@ def _lib():
         lib.ys_assign_noalloc.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog)]
         lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
         lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
+        lib.ys_plan_autotune.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), ctypes.c_int32,
+                                         ctypes.POINTER(YsTuning)]
+        lib.ys_batch_create.argtypes = [ctypes.POINTER(YsConfig), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(P)]
+        lib.ys_batch_result_stride.argtypes = [P]
+        lib.ys_batch_result_stride.restype = ctypes.c_int64
+        lib.ys_batch_autotune.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), ctypes.c_int32]
+        lib.ys_batch_run.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), P, P]
+        lib.ys_batch_destroy.argtypes = [P]
         lib.ys_status_string.argtypes = [ctypes.c_int]
         lib.ys_status_string.restype = ctypes.c_char_p
         lib.ys_last_cuda_error.restype = ctypes.c_char_p
         for name in ("ys_plan_create", "ys_assign", "ys_measure_multipoles_async",
                      "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
-                     "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc"):
+                     "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc", "ys_plan_autotune",
+                     "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -156,6 +171,40 @@ def _ptr(a):
     return a.ctypes.data
 
 
+def make_config(n_mesh, box_min, box_len, observer=(0.0, 0.0, 0.0), assign="cic", interlace=False,
+                compensate=True, ell_max=4, k_min=0.0, dk=0.01, n_bins=None, k_max=None, alpha=-1.0,
+                max_particles=0, stream=None):
+    """A filled ys_config (shells of width dk from k_min up to k_max, default Nyquist)."""
+    if n_bins is None:
+        kmax = k_max if k_max is not None else np.pi * n_mesh / box_len
+        n_bins = int(np.ceil((kmax - k_min) / dk - 1e-9))
+    cfg = YsConfig()
+    cfg.n_mesh = n_mesh
+    cfg.box_min = (ctypes.c_double * 3)(*box_min)
+    cfg.box_len = box_len
+    cfg.observer = (ctypes.c_double * 3)(*observer)
+    cfg.assign = ASSIGN[assign] if isinstance(assign, str) else int(assign)
+    cfg.interlace = int(bool(interlace))
+    cfg.compensate = int(bool(compensate))
+    cfg.ell_max = ell_max
+    cfg.k_min = k_min
+    cfg.dk = dk
+    cfg.n_bins = n_bins
+    cfg.alpha = alpha
+    cfg.max_particles = int(max_particles)
+    cfg.stream = stream
+    return cfg
+
+
+def parse_row(row, n_bins):
+    """Split one result row [k | n_modes | p0 | p2 | p4 | alpha, I, S/I, n_out, timeout]."""
+    row = np.asarray(row, dtype=np.float64)
+    nb = n_bins
+    return Result(row[:nb], row[nb:2 * nb], row[2 * nb:3 * nb], row[3 * nb:4 * nb], row[4 * nb:5 * nb],
+                  float(row[5 * nb]), float(row[5 * nb + 1]), float(row[5 * nb + 2]),
+                  YS_ERR_TIMEOUT if row[5 * nb + 4] != 0 else (YS_ERR_ARG if row[5 * nb + 3] > 0 else YS_OK))
+
+
 class Plan:
     """One estimator configuration on the current CUDA device (ys_plan)."""
 
@@ -163,24 +212,9 @@ class Plan:
                  interlace=False, compensate=True, ell_max=4, k_min=0.0, dk=0.01, n_bins=None,
                  k_max=None, alpha=-1.0, max_particles=0, stream=None):
         lib = _lib()
-        if n_bins is None:
-            kmax = k_max if k_max is not None else np.pi * n_mesh / box_len
-            n_bins = int(np.ceil((kmax - k_min) / dk - 1e-9))
-        cfg = YsConfig()
-        cfg.n_mesh = n_mesh
-        cfg.box_min = (ctypes.c_double * 3)(*box_min)
-        cfg.box_len = box_len
-        cfg.observer = (ctypes.c_double * 3)(*observer)
-        cfg.assign = ASSIGN[assign] if isinstance(assign, str) else int(assign)
-        cfg.interlace = int(bool(interlace))
-        cfg.compensate = int(bool(compensate))
-        cfg.ell_max = ell_max
-        cfg.k_min = k_min
-        cfg.dk = dk
-        cfg.n_bins = n_bins
-        cfg.alpha = alpha
-        cfg.max_particles = int(max_particles)
-        cfg.stream = stream
+        cfg = make_config(n_mesh, box_min, box_len, observer, assign, interlace, compensate, ell_max, k_min,
+                          dk, n_bins, k_max, alpha, max_particles, stream)
+        n_bins = cfg.n_bins
         self.cfg = cfg
         self.n_bins = n_bins
         h = ctypes.c_void_p()
@@ -233,6 +267,14 @@ class Plan:
                     "ys_estimate_host")
         return Result(*arrs, res.alpha, res.norm_I, res.shot_noise, st)
 
+    def autotune(self, gal, ran, reps=3):
+        """ys_plan_autotune on device catalogues; returns the chosen YsTuning."""
+        g, r, t = self._cat(*gal), self._cat(*ran), YsTuning()
+        self._keep = (gal, ran)
+        _check(_lib().ys_plan_autotune(self._h, ctypes.byref(g), ctypes.byref(r), reps, ctypes.byref(t)),
+               "ys_plan_autotune")
+        return t
+
     def set_profiling(self, enable: bool):
         _check(_lib().ys_plan_set_profiling(self._h, int(bool(enable))), "ys_plan_set_profiling")
 
@@ -245,6 +287,59 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib().ys_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """ys_batch: many catalogues (mixed configurations) in one graph launch."""
+
+    def __init__(self, configs, branches=4):
+        lib = _lib()
+        n = len(configs)
+        arr = (YsConfig * n)(*configs)
+        h = ctypes.c_void_p()
+        _check(lib.ys_batch_create(arr, n, branches, ctypes.byref(h)), "ys_batch_create")
+        self._h = h
+        self.n = n
+        self.n_bins = [c.n_bins for c in configs]
+        self.stride = int(lib.ys_batch_result_stride(h))
+        self._keep = None
+
+    @staticmethod
+    def _cats(cats):
+        arr = (YsCatalog * len(cats))()
+        for i, c in enumerate(cats):
+            arr[i] = Plan._cat(*c)
+        return arr
+
+    def autotune(self, gals, rans, reps=2):
+        _check(_lib().ys_batch_autotune(self._h, self._cats(gals), self._cats(rans), reps), "ys_batch_autotune")
+
+    def run(self, gals, rans, d_results, stream=None):
+        """gals, rans: lists of device tensor tuples; d_results: device float64 (n, stride)."""
+        self._keep = (gals, rans, d_results)
+        self._g, self._r = self._cats(gals), self._cats(rans)
+        _check(_lib().ys_batch_run(self._h, self._g, self._r, _ptr(d_results), stream), "ys_batch_run")
+
+    def results(self, d_results):
+        host = d_results.cpu().numpy() if hasattr(d_results, "cpu") else np.asarray(d_results)
+        return [parse_row(host[i], self.n_bins[i]) for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().ys_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

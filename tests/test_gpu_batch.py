@@ -1,0 +1,93 @@
+"""Batched runs (one graph launch over catalogues of mixed size and mesh) and the
+autotuner: every row equals the same catalogue run alone, within the parity bar,
+and the oracle; replaying the captured graph reproduces the rows."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.binning import BinSpec
+
+torch = pytest.importorskip("torch")
+ys = pytest.importorskip("paper_1505_05341_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def dev(c):
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (c.x, c.y, c.z, c.w, c.nbar))
+
+
+def close_rows(a, b, label):
+    np.testing.assert_array_equal(a.n_modes, b.n_modes)
+    has = a.n_modes > 0
+    raw = a.p0 + a.shot_noise
+    for l in (0, 2, 4):
+        x, y = getattr(a, f"p{l}"), getattr(b, f"p{l}")
+        sel = has & (np.abs(x) > 1e-2 * np.abs(raw))
+        if sel.any():
+            assert np.max(np.abs(y[sel] - x[sel]) / np.abs(x[sel])) <= TOL, (label, l)
+
+
+def batch_inputs():
+    meshes = [32, 64, 96, 128, 64, 32, 96, 128]
+    kinds = ["cic", "tsc", "cic", "cic", "ngp", "tsc", "tsc", "cic"]
+    cats, cfgs = [], []
+    for i, (n, kind) in enumerate(zip(meshes, kinds)):
+        ng = 3000 + 1500 * i
+        gal, ran, geo = synth.poisson_cube(ng, 5 * ng, seed=300 + i)
+        il = kind == "tsc"
+        cfgs.append(ys.make_config(n, geo.box_min, geo.box_len, geo.observer, assign=kind, interlace=il, dk=0.01,
+                                   max_particles=6 * ng))
+        cats.append((gal, ran, geo, n, kind, il))
+    return cats, cfgs
+
+
+def test_batch_rows_equal_single_runs_and_oracle():
+    cats, cfgs = batch_inputs()
+    gals = [dev(c[0]) for c in cats]
+    rans = [dev(c[1]) for c in cats]
+    with ys.Batch(cfgs, branches=3) as batch:
+        out = torch.zeros((batch.n, batch.stride), dtype=torch.float64, device="cuda")
+        batch.run(gals, rans, out)
+        torch.cuda.synchronize()
+        rows = batch.results(out)
+        out2 = torch.zeros_like(out)
+        batch.run(gals, rans, out2)  # pointers changed -> recapture
+        batch.run(gals, rans, out2)  # replay
+        torch.cuda.synchronize()
+        rows2 = batch.results(out2)
+    for i, (gal, ran, geo, n, kind, il) in enumerate(cats):
+        with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign=kind, interlace=il, dk=0.01) as plan:
+            plan.assign(gals[i], rans[i])
+            single = plan.measure()
+        assert rows[i].status == 0
+        close_rows(single, rows[i], f"batch row {i}")
+        close_rows(single, rows2[i], f"replayed row {i}")
+    gal, ran, geo, n, kind, il = cats[2]
+    bins = BinSpec.up_to(np.pi * n / geo.box_len, 0.01)
+    ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign=kind, interlace=il)
+    np.testing.assert_array_equal(rows[2].n_modes, ref.n_modes)
+    has = ref.n_modes > 0
+    raw = ref.sum0[has] / ref.n_modes[has] / ref.norm.I
+    for l in (0, 2, 4):
+        g, o = getattr(rows[2], f"p{l}")[has], getattr(ref, f"p{l}")[has]
+        sel = np.abs(o) > 1e-2 * raw
+        assert np.max(np.abs(g[sel] - o[sel]) / np.abs(o[sel])) <= TOL
+
+
+def test_autotune_keeps_results():
+    gal, ran, geo = synth.poisson_cube(30_000, 150_000, side=1000.0, center=(0.0, 0.0, 0.0), seed=77)
+    g, r = dev(gal), dev(ran)
+    with ys.Plan(128, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, dk=0.01) as plan:
+        plan.assign(g, r)
+        before = plan.measure()
+        t = plan.autotune(g, r, reps=2)
+        assert all(v > 0 for v in t.tile) and t.yz_grid > 0 and t.measure_ms > 0
+        after_tune = plan.measure()
+        plan.assign(g, r)
+        after = plan.measure()
+    close_rows(before, after_tune, "autotune state")
+    close_rows(before, after, "after autotune")
