@@ -240,6 +240,72 @@ ys_status ys_batch_run(ys_batch* batch, const ys_catalog* gal, const ys_catalog*
 /* Free the batch and its plans.  NULL is accepted. */
 ys_status ys_batch_destroy(ys_batch* batch);
 
+/* ---- Learned aliasing/window correction (no counterpart in the paper: the paper
+ * notes that mesh aliasing is what separates its FFT estimate from the galaxy sum at
+ * high k, and this network estimates that residual from a coarse measurement) ----
+ *
+ * Network: x (5) -> 64 -> 64 -> 64 -> 3, GELU (erf form) after each hidden layer,
+ * linear output.  Parameters are a flat float vector of YS_MLP_PARAMS values,
+ * row-major weights W[out][in] then bias for each layer in order:
+ *   W1[64][5] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[3][64] b4[3].
+ * The kernels use a bfloat16 copy of the weights (round to nearest even) and FP32
+ * activations and accumulation; Adam updates an FP32 master copy.
+ *
+ * Per-shell features of a result row (layout of ys_measure_multipoles_async), with
+ * D = P_0 + S/I the coarse monopole before shot-noise subtraction:
+ *   x = [ k_mean / k_nyq, ln(D / (S/I)), P_2 / D, P_4 / D, (S/I) / D ]
+ * Targets, given a fine-mesh row of the same catalogue and binning:
+ *   t_l = (P_l^fine - P_l^coarse) / D,  l = 0, 2, 4.
+ * Correction: P_l <- P_l + D y_l for every shell with modes.
+ * Row layout of X: rows x 5 floats; of Y and T: rows x 3 floats (DEVICE). */
+#define YS_MLP_PARAMS 8899
+typedef struct ys_mlp_s ys_mlp;
+
+/* Create a network on the current device from h_params (HOST, YS_MLP_PARAMS floats);
+ * Adam moments start at zero.  Synchronous. */
+ys_status ys_mlp_create(const float* h_params, ys_mlp** out);
+
+/* Copy the FP32 master parameters, and optionally the Adam moments m, v (HOST,
+ * YS_MLP_PARAMS floats each, may be NULL) and the step count, to the host.
+ * Synchronous. */
+ys_status ys_mlp_get_state(ys_mlp* mlp, float* h_params, float* h_m, float* h_v, int64_t* h_step);
+
+/* Restore a state saved by ys_mlp_get_state (h_m, h_v NULL: zero moments). */
+ys_status ys_mlp_set_state(ys_mlp* mlp, const float* h_params, const float* h_m, const float* h_v, int64_t step);
+
+/* Y = net(X) for `rows` rows (DEVICE pointers).  Asynchronous on stream. */
+ys_status ys_mlp_forward(ys_mlp* mlp, const float* d_x, int64_t rows, float* d_y, void* stream);
+
+/* Gradient of loss = sum over rows and outputs of (y - t)^2 / (3 rows) with respect
+ * to the parameters, at the bfloat16 weights, into d_grad (DEVICE, YS_MLP_PARAMS
+ * floats, may be NULL) and the summed squared error into d_sse (DEVICE, one double,
+ * may be NULL).  rows >= 1.  Asynchronous. */
+ys_status ys_mlp_gradient(ys_mlp* mlp, const float* d_x, const float* d_t, int64_t rows, float* d_grad,
+                          double* d_sse, void* stream);
+
+/* One full-batch Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
+ * the gradient above; refreshes the bfloat16 copy.  d_sse as above.  Asynchronous. */
+ys_status ys_mlp_train_step(ys_mlp* mlp, const float* d_x, const float* d_t, int64_t rows, float lr,
+                            double* d_sse, void* stream);
+
+/* Features (and, if d_fine_rows != NULL, targets) of n_cat result rows spaced
+ * `stride` doubles apart (DEVICE).  A shell enters when it has modes and finite
+ * multipoles; d_src[j] = catalogue * n_bins + shell of feature row j and *d_count =
+ * number of rows written (DEVICE int32; the order of rows is not fixed).  d_x needs
+ * n_cat n_bins x 5 floats, d_t n_cat n_bins x 3, d_src n_cat n_bins.  Asynchronous. */
+ys_status ys_mlp_features(const double* d_rows, const double* d_fine_rows, int32_t n_cat, int64_t stride,
+                          int32_t n_bins, double k_nyq, float* d_x, float* d_t, int32_t* d_src, int32_t* d_count,
+                          void* stream);
+
+/* Corrected result rows: d_out (DEVICE, same layout; may equal d_rows) receives
+ * d_rows with P_l + D y_l in every shell with modes.  Asynchronous; the first call
+ * for a larger n_cat * n_bins allocates feature scratch. */
+ys_status ys_mlp_correct(ys_mlp* mlp, const double* d_rows, int32_t n_cat, int64_t stride, int32_t n_bins,
+                         double k_nyq, double* d_out, void* stream);
+
+/* Free the network.  NULL is accepted. */
+ys_status ys_mlp_destroy(ys_mlp* mlp);
+
 /* Static description of a status code. */
 const char* ys_status_string(ys_status s);
 

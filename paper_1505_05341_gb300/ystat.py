@@ -120,13 +120,26 @@ def _lib():
         lib.ys_batch_autotune.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), ctypes.c_int32]
         lib.ys_batch_run.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), P, P]
         lib.ys_batch_destroy.argtypes = [P]
+        F, D, I64 = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+        lib.ys_mlp_create.argtypes = [F, ctypes.POINTER(P)]
+        lib.ys_mlp_get_state.argtypes = [P, F, F, F, ctypes.POINTER(I64)]
+        lib.ys_mlp_set_state.argtypes = [P, F, F, F, I64]
+        lib.ys_mlp_forward.argtypes = [P, P, I64, P, P]
+        lib.ys_mlp_gradient.argtypes = [P, P, P, I64, P, P, P]
+        lib.ys_mlp_train_step.argtypes = [P, P, P, I64, ctypes.c_float, P, P]
+        lib.ys_mlp_features.argtypes = [P, P, ctypes.c_int32, I64, ctypes.c_int32, ctypes.c_double, P, P, P, P, P]
+        lib.ys_mlp_correct.argtypes = [P, P, ctypes.c_int32, I64, ctypes.c_int32, ctypes.c_double, P, P]
+        lib.ys_mlp_destroy.argtypes = [P]
         lib.ys_status_string.argtypes = [ctypes.c_int]
         lib.ys_status_string.restype = ctypes.c_char_p
         lib.ys_last_cuda_error.restype = ctypes.c_char_p
         for name in ("ys_plan_create", "ys_assign", "ys_measure_multipoles_async",
                      "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
                      "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc", "ys_plan_autotune",
-                     "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy"):
+                     "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy",
+                     "ys_mlp_create", "ys_mlp_get_state", "ys_mlp_set_state", "ys_mlp_forward",
+                     "ys_mlp_gradient", "ys_mlp_train_step", "ys_mlp_features", "ys_mlp_correct",
+                     "ys_mlp_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -340,6 +353,84 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib().ys_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+MLP_PARAMS = 8899
+
+
+def _fptr(a):
+    return ctypes.cast(a.ctypes.data, ctypes.POINTER(ctypes.c_float)) if a is not None else None
+
+
+class Mlp:
+    """ys_mlp: the learned aliasing/window correction network (device-resident).
+
+    Device arrays are torch CUDA tensors (or anything with ``data_ptr``); feature rows
+    are float32 (rows, 5), targets/outputs float32 (rows, 3), result rows float64."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters, got {p.size}")
+        h = ctypes.c_void_p()
+        _check(_lib().ys_mlp_create(_fptr(p), ctypes.byref(h)), "ys_mlp_create")
+        self._h = h
+
+    def state(self):
+        """(params, m, v, step) on the host."""
+        w, m, v = (np.empty(MLP_PARAMS, np.float32) for _ in range(3))
+        t = ctypes.c_int64()
+        _check(_lib().ys_mlp_get_state(self._h, _fptr(w), _fptr(m), _fptr(v), ctypes.byref(t)), "ys_mlp_get_state")
+        return w, m, v, int(t.value)
+
+    def params(self):
+        return self.state()[0]
+
+    def set_state(self, params, m=None, v=None, step=0):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, m, v)]
+        _check(_lib().ys_mlp_set_state(self._h, *(_fptr(a) for a in arrs), int(step)), "ys_mlp_set_state")
+
+    def forward(self, d_x, d_y, rows=None, stream=None):
+        rows = d_x.shape[0] if rows is None else rows
+        _check(_lib().ys_mlp_forward(self._h, _ptr(d_x), rows, _ptr(d_y), stream), "ys_mlp_forward")
+
+    def gradient(self, d_x, d_t, d_grad=None, d_sse=None, rows=None, stream=None):
+        rows = d_x.shape[0] if rows is None else rows
+        _check(_lib().ys_mlp_gradient(self._h, _ptr(d_x), _ptr(d_t), rows, _ptr(d_grad), _ptr(d_sse), stream),
+               "ys_mlp_gradient")
+
+    def train_step(self, d_x, d_t, lr, d_sse=None, rows=None, stream=None):
+        rows = d_x.shape[0] if rows is None else rows
+        _check(_lib().ys_mlp_train_step(self._h, _ptr(d_x), _ptr(d_t), rows, float(lr), _ptr(d_sse), stream),
+               "ys_mlp_train_step")
+
+    @staticmethod
+    def features(d_rows, n_bins, k_nyq, d_x, d_src, d_count, d_fine_rows=None, d_t=None, stream=None):
+        n_cat, stride = d_rows.shape
+        _check(_lib().ys_mlp_features(_ptr(d_rows), _ptr(d_fine_rows), n_cat, stride, n_bins, float(k_nyq),
+                                      _ptr(d_x), _ptr(d_t), _ptr(d_src), _ptr(d_count), stream), "ys_mlp_features")
+
+    def correct(self, d_rows, n_bins, k_nyq, d_out, stream=None):
+        n_cat, stride = d_rows.shape
+        _check(_lib().ys_mlp_correct(self._h, _ptr(d_rows), n_cat, stride, n_bins, float(k_nyq), _ptr(d_out),
+                                     stream), "ys_mlp_correct")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().ys_mlp_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
