@@ -82,7 +82,7 @@ class ClockSampler:
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -256,6 +256,11 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        # keep the GPU busy while nvidia-smi starts, so that its samples fall under load
+        t_spin = time.perf_counter() + 0.6
+        while time.perf_counter() < t_spin:
+            step()
+            torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
             step()
@@ -334,6 +339,9 @@ def run_ours(args):
         plan.close()
         torch.cuda.empty_cache()
         line["batched"] = run_batched(max(1, min(args.steps, 3)), 1)
+    if world == 1 and not args.no_learned and args.workload == WORKLOAD:
+        line["learned"] = run_learned(max(1, min(args.steps, 3)))
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_cat, sample, cores = cpu_sample(gal, ran, geo)
         line["cpu_baseline"] = {"value": 1.0 / per_cat, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -347,26 +355,17 @@ def run_ours(args):
 
 def batched_catalogues(n_cat=256, first_seed=1000):
     """The batched-mock workload on the GPU: per catalogue (seed, n_gal, mesh) from
-    synth.batched_cube_specs; uniform points in the 500 Mpc/h cube centred on
-    (600, 600, 600), observer at the origin, unit weights, nbar = n_gal / 500^3; the
-    points are drawn on the device from a generator seeded with the catalogue seed."""
-    import torch
+    synth.batched_cube_specs; config-1-style clustered mocks (Zel'dovich + RSD in the
+    500 Mpc/h cube centred on (600, 600, 600), observer at the origin, randoms 5 n_gal,
+    unit weights) drawn on the device from generators seeded with the catalogue seed."""
     import synth
+    import synth.gpu as sg
     specs = synth.batched_cube_specs(n_cat, first_seed)
-    lo, side = 350.0, 500.0
     gals, rans = [], []
     for seed, ng, nr, mesh in specs:
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(seed)
-        nbar = ng / side ** 3
-        cats = []
-        for n in (ng, nr):
-            p = lo + side * torch.rand((3, n), generator=gen, device="cuda", dtype=torch.float64)
-            p = p.to(torch.float32).clamp_(max=float(np.nextafter(np.float32(lo + side), np.float32(0))))
-            cats.append((p[0].contiguous(), p[1].contiguous(), p[2].contiguous(),
-                         torch.ones(n, device="cuda"), torch.full((n,), nbar, device="cuda")))
-        gals.append(cats[0])
-        rans.append(cats[1])
+        g, r, _ = sg.zeldovich_cube(ng, nr, seed)
+        gals.append(g)
+        rans.append(r)
     return specs, gals, rans
 
 
@@ -425,6 +424,87 @@ def run_batched(steps, warmup):
             "particles": int(sum(g + r for s_, g, r, m in specs))}
 
 
+def run_learned(steps, n_heldout=200):
+    """Learned correction on the held-out mocks (seeds 20000-20199): the coarse 128^3
+    CIC measurement of every mock in one batched graph launch plus one correction
+    launch, against the plain 512^3 TSC+interlaced path on the same mocks, with the
+    residual of both coarse and corrected multipoles against the 512^3 result."""
+    import torch
+    import paper_1505_05341_gb300 as ys
+    import synth.gpu as sg
+    from paper_1505_05341_gb300 import learned
+    if not os.path.exists(learned.WEIGHTS):
+        return {"unavailable": "no trained weights at " + os.path.relpath(learned.WEIGHTS, ROOT)}
+    mlp, meta = learned.load()
+    seeds = list(range(learned.HELDOUT_SEEDS, learned.HELDOUT_SEEDS + n_heldout))
+    gals, rans, caps = [], [], []
+    for sd in seeds:
+        ng, nr = sg.mock_sizes(sd)
+        g, r, _ = sg.zeldovich_cube(ng, nr, sd)
+        gals.append(g)
+        rans.append(r)
+        caps.append(ng + nr)
+    n = len(seeds)
+    cfgs = [ys.make_config(learned.COARSE["n_mesh"], learned.BOX_MIN, learned.BOX_LEN, learned.OBSERVER,
+                           assign=learned.COARSE["assign"], interlace=learned.COARSE["interlace"], dk=learned.DK,
+                           n_bins=learned.N_BINS, max_particles=c) for c in caps]
+    batch = ys.Batch(cfgs, branches=4)
+    rows = torch.zeros((n, batch.stride), dtype=torch.float64, device="cuda")
+    corr = torch.empty_like(rows)
+    batch.autotune(gals, rans, reps=2)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def learned_pass():
+        batch.run(gals, rans, rows, sp)
+        mlp.correct(rows, learned.N_BINS, learned.K_NYQ, corr, sp)
+
+    for _ in range(2):
+        learned_pass()
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(steps):
+        learned_pass()
+    e1.record(stream)
+    for _ in range(steps):
+        mlp.correct(rows, learned.N_BINS, learned.K_NYQ, corr, sp)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ms_learned = e0.elapsed_time(e1) / steps
+    ms_mlp = e1.elapsed_time(e2) / steps
+    batch.close()
+    # plain 512^3 path on the same mocks: the target of the correction and the comparison
+    fine = ys.Plan(learned.FINE["n_mesh"], learned.BOX_MIN, learned.BOX_LEN, learned.OBSERVER,
+                   assign=learned.FINE["assign"], interlace=learned.FINE["interlace"], dk=learned.DK,
+                   n_bins=learned.N_BINS, max_particles=max(caps), stream=sp)
+    rows_f = torch.zeros_like(rows)
+    fine.assign(gals[0], rans[0])
+    fine.measure_async(rows_f[0])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(n):
+        fine.assign(gals[i], rans[i])
+        fine.measure_async(rows_f[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fine = e0.elapsed_time(e1)
+    fine.close()
+    before = learned.residual_stats(rows, rows_f)
+    after = learned.residual_stats(corr, rows_f)
+    mlp.close()
+    return {"value": n / (ms_learned / 1e3), "unit": UNIT, "n_catalogs": n, "ms_per_pass": ms_learned,
+            "mlp_ms_per_pass": ms_mlp, "plain_512_value": n / (ms_fine / 1e3),
+            "speedup_vs_plain_512": ms_fine / ms_learned,
+            "residual_vs_512": {"uncorrected_128": before, "corrected_128": after,
+                                "definition": "|P_l - P_l(512^3)| / (P_0 + S/I) over shells with modes, "
+                                              "k < 0.80 h/Mpc; rms and max"},
+            "coarse": "128^3 CIC, no interlacing, batched (4 branches)",
+            "fine": "512^3 TSC, interlaced, plain path",
+            "heldout_seeds": [seeds[0], seeds[-1]],
+            "trained": {k: meta[k] for k in ("train_seeds", "rows", "steps", "lr", "lr_final")}}
+
+
 def plan_pencils(plan):
     """Number of (k_y, k_z) pencils the plan keeps: k_y^2 + k_z^2 < n2_hi, derived
     from the shell edges exactly as the library does (integer |m|^2 test)."""
@@ -450,11 +530,12 @@ def plan_pencils(plan):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":
