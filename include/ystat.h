@@ -197,18 +197,21 @@ ys_status ys_plan_destroy(ys_plan* plan);
 /* ---- Autotuning and batched runs (throughput arrangements; no counterpart in the
  * paper's equations, which these calls evaluate unchanged) ---- */
 
-/* Launch shapes the autotuner chose: scatter tile (nodes per axis) and CTAs of the
- * persistent y,z kernel, with the best measured times. */
+/* Launch shapes the autotuner chose: scatter tile (nodes per axis), CTAs of the
+ * persistent y,z kernel and the lead (in x-planes) of its column items over its row
+ * items, with the best measured times. */
 typedef struct {
   int32_t tile[3];
   int32_t yz_grid;
+  int32_t ring_lead;
   double assign_ms;
   double measure_ms;
 } ys_tuning;
 
-/* Time the candidate scatter tiles (16x16x32, 8x16x32, 16x16x16, 32x16x32, 8x8x32)
- * and y,z grids (resident, 3/4, 1/2) on this catalogue (DEVICE pointers), reps timed
- * calls each, and keep the fastest in the plan.  Leaves the catalogue assigned.
+/* Time the candidate scatter tiles (16x16x32, 8x16x32, 16x16x16, 32x16x32, 8x8x32),
+ * y,z grids (resident, 3/4, 1/2) and ring leads (0.7x, 1x, 1.4x, 2x a work-balanced
+ * estimate) on this catalogue (DEVICE pointers), reps timed calls each, and keep the
+ * fastest in the plan.  Leaves the catalogue assigned.
  * Synchronous.  out may be NULL. */
 ys_status ys_plan_autotune(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran, int32_t reps,
                            ys_tuning* out);

@@ -285,10 +285,26 @@ void set_tiles(Plan& p, int tx, int ty, int tz) {
   }
 }
 
-void set_yz_grid(Plan& p, int grid) {
+// Lead D of the y,z ring: the column items of plane p are claimed D planes after its
+// row items, and must not be claimed before those finish (a claimed item that waits
+// idles its CTA).  Between the two claims the grid works through about
+// D * W_plane - (grid - NZ) * w_row of other items, with W_plane = NZ w_row + NY w_col
+// the work of one plane's items in FFT-line units (a row item: R rows x field pairs,
+// plus field construction; a column item: its basis fields plus the fold).
+int ring_lead_for(const Plan& p, int grid, int pct) {
+  const int nz = yz_row_items(p.n), ny = std::max(1, p.nzc);
+  const double rows = (double)p.n / nz;
+  const double w_row = rows * ((p.nb + 1) / 2) * 1.3, w_col = p.nb * 1.2;
+  const double plane = nz * w_row + ny * w_col;
+  const double base = std::ceil(std::max(0, grid - nz) * w_row / plane) + 1.0;
+  return std::max(2, (int)std::ceil(base * pct / 100.0));
+}
+
+void set_yz_grid(Plan& p, int grid, int lead_pct) {
   p.yz_grid = std::max(1, std::min(grid, p.yz_grid_max));
-  const int items_per_plane = yz_row_items(p.n) + std::max(1, p.nzc);
-  p.ring_lead = (p.yz_grid + items_per_plane - 1) / items_per_plane + 1;
+  if (lead_pct > 0) p.ring_lead_pct = lead_pct;
+  const int slots_max = p.ring_slots_cap > 0 ? p.ring_slots_cap : p.m * p.n;
+  p.ring_lead = std::min(ring_lead_for(p, p.yz_grid, p.ring_lead_pct), std::max(1, slots_max - 2));
   p.ring_slots = std::min(p.m * p.n, p.ring_lead + 2);
 }
 
@@ -327,7 +343,7 @@ cudaError_t launch_finalize(Plan& p) {
 
 // Row items per plane of the y,z kernel (N / rows per item; mirrors YZ<N, ELL>::R).
 int yz_row_items(int n) {
-  const int E = (n & (n - 1)) == 0 ? (n >= 512 ? 16 : 8) : (n >= 768 ? 24 : 12);
+  const int E = (n & (n - 1)) == 0 ? 8 : 12;  // fft_elems
   const int lpp = 256 / (n / E);
   const int base = n >= 512 ? 8 : 16;
   const int r = lpp > base ? std::min(lpp, n) : base;
@@ -448,9 +464,12 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
     delete h;
     return st;
   }
-  ys::set_yz_grid(p, p.yz_grid_max);  // ring sized for the largest grid
+  // ring sized for the largest grid and lead the tuner may pick
+  ys::set_yz_grid(p, p.yz_grid_max, ys::kRingLeadPctMax);
+  p.ring_slots_cap = p.ring_slots;
+  ys::set_yz_grid(p, p.yz_grid_max, 100);
   const size_t slot = (size_t)p.nb * std::max(1, p.nzc) * n;
-  if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, slot * p.ring_slots)) ||
+  if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, slot * p.ring_slots_cap)) ||
       (e = ys::dalloc(p, p.d_sync, (size_t)2 * p.m * n + 2)) ||
       (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np_pad))) ||
       (e = ys::dalloc(p, p.d_acc, (size_t)3 * c.n_bins)) || (e = ys::dalloc(p, p.d_sums, (size_t)ys::SUM_COUNT)) ||

@@ -159,10 +159,6 @@ struct YZ {
   static_assert(N % R == 0, "rows per item must divide N");
 };
 
-template <int N>
-__device__ __forceinline__ void line_sync() {
-  if constexpr (N / fft_elems(N) <= 32) __syncwarp(); else __syncthreads();
-}
 
 // One pair of basis fields (fa = 2 pr, fb = 2 pr + 1) for the R rows of a row item:
 // fields at the nodes (first FFT stage from registers, one butterfly at a time),
@@ -209,7 +205,7 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restr
       }
     }
   }
-  line_sync<N>();
+  line_group_sync<TPL>();  // each line is written and read by its own threads
   FftRun<N, 1, false, true, R>::run(C, 1, LL, R, tw);
   __syncthreads();
   for (int e = threadIdx.x; e < nzc * R; e += blockDim.x) {
@@ -271,7 +267,7 @@ __device__ __forceinline__ void column_item(float2* S, const float2* __restrict_
       fft_stage0_regs<N, true>(v, S + f * LL, 1, tl);
     }
   }
-  line_sync<N>();
+  line_group_sync<TPL>();  // each line is written and read by its own threads
   FftRun<N, 1, false, true, NB>::run(S, 1, LL, NB, tw);
   __syncthreads();
   column_fold<N, ELL>(S, kz, col_off, gout, j, ix, np);

@@ -89,6 +89,22 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
     }
   }
   set_yz_grid(p, best_grid);
+  // 3. lead of the y,z ring at that grid
+  int best_pct = p.ring_lead_pct;
+  for (int pct : {70, 140, kRingLeadPctMax}) {
+    set_yz_grid(p, best_grid, pct);
+    float ms = 0.f;
+    e = time_ms(p, reps, [&] { return launch_measure(p); }, &ms);
+    if (e) {
+      why = cudaGetErrorString(e);
+      return YS_ERR_CUDA;
+    }
+    if (ms < best_measure) {
+      best_measure = ms;
+      best_pct = pct;
+    }
+  }
+  set_yz_grid(p, best_grid, best_pct);
   // the captured measurement graph holds the old launch shapes
   if (p.measure_exec) {
     cudaGraphExecDestroy(p.measure_exec);
@@ -101,6 +117,7 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
   if (out) {
     for (int a = 0; a < 3; ++a) out->tile[a] = p.geom.tdim[a];
     out->yz_grid = p.yz_grid;
+    out->ring_lead = p.ring_lead;
     out->assign_ms = best_assign;
     out->measure_ms = best_measure;
   }

@@ -50,6 +50,8 @@ struct Plan {
   int np_pad = 0;                // np rounded up to whole x-stage pencil blocks
   int ring_slots = 1;            // S: planes held by the y,z-stage ring
   int ring_lead = 1;             // D: column items trail row items by D planes
+  int ring_lead_pct = 100;       // D relative to the work-balanced estimate (tuned)
+  int ring_slots_cap = 0;        // ring slots allocated
   int yz_grid = 1;               // CTAs of the persistent y,z kernel
   int yz_grid_max = 1;           // resident CTAs of that kernel (upper bound for tuning)
   int ntiles_max = 0;            // tile-counter capacity over the scatter tile candidates
@@ -113,7 +115,8 @@ cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran)
 // Scatter tile shape (nodes per axis, capped at N); updates geom and ntiles.
 void set_tiles(Plan& p, int tx, int ty, int tz);
 // y,z grid size; updates the ring lead D and slots S (S never exceeds the allocation).
-void set_yz_grid(Plan& p, int grid);
+void set_yz_grid(Plan& p, int grid, int lead_pct = 0);
+constexpr int kRingLeadPctMax = 200;
 ys_status ensure_particles(Plan& p, int64_t total);
 extern thread_local std::string g_last_cuda_error;
 cudaError_t launch_measure(Plan& p);
