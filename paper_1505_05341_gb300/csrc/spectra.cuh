@@ -31,57 +31,33 @@ namespace ys {
 
 #include "group_table.inc"
 
+// Basis fields at the nodes.  A field is F times r_hat_x^a r_hat_y^b r_hat_z^c of
+// degree d = a + b + c in {2, 4} (c <= 1), or F itself (d = 0), or F without the
+// node at r = 0 (d = -1), or nothing (d = -2, past the last field).  With
+// r = (X, Y, Z) from the observer, r_hat^(a,b,c) = X^a Y^b Z^c / |r|^d, and along one
+// z-line X and Y are fixed: K = X^a Y^b is one number per line and field, so a node
+// costs one reciprocal of |r|^2 shared by all fields plus two or three products per
+// field.
 
-template <int A>
-__device__ __forceinline__ float ipow(float v) {
-  float r = 1.f;
-#pragma unroll
-  for (int i = 0; i < A; ++i) r *= v;
+// v^e for a small run-time exponent 0 <= e <= 4 (warp-uniform).
+__device__ __forceinline__ float ipow_rt(float v, int e) {
+  const float v2 = v * v;
+  float r = (e & 1) ? v : 1.f;
+  if (e >= 2) r *= v2;
+  if (e >= 4) r *= v2;
   return r;
 }
 
-// Value at one node of a basis field given by its exponents (a, b, c) and degree d
-// (uniform across the warp): d = 0 -> F, d = -1 -> F without the r = 0 node,
-// d = -2 -> none (0), else F r_hat_x^a r_hat_y^b r_hat_z^c with a, b <= 4, c <= 1.
-__device__ __forceinline__ float basis_value_rt(float f, float xh, float yh, float zh, bool nonzero_r, int a, int b,
-                                                int c, int d) {
+// Field value at a node: f the mesh value, i2 = 1/|r|^2 (0 where r = 0), z = Z, K the
+// line constant X^a Y^b; c, d warp-uniform.
+__device__ __forceinline__ float basis_value_rt(float f, float i2, float z, float K, int c, int d) {
   if (d == 0) return f;
-  if (d == -1) return nonzero_r ? f : 0.f;
+  if (d == -1) return i2 > 0.f ? f : 0.f;
   if (d == -2) return 0.f;
-  float v = f;
-  if (a >= 1) v *= xh;
-  if (a >= 2) v *= xh;
-  if (a >= 3) v *= xh;
-  if (a >= 4) v *= xh;
-  if (b >= 1) v *= yh;
-  if (b >= 2) v *= yh;
-  if (b >= 3) v *= yh;
-  if (b >= 4) v *= yh;
-  if (c >= 1) v *= zh;
+  float v = (f * K) * i2;
+  if (d == 4) v *= i2;
+  if (c) v *= z;
   return v;
-}
-
-// Value of basis field BETA at one node (compile-time exponents; 0 past the last field).
-template <int ELL, int BETA>
-__device__ __forceinline__ float basis_value(float f, float xh, float yh, float zh, bool nonzero_r) {
-  if constexpr (BETA >= GroupTable<ELL>::NB) {
-    return 0.f;
-  } else {
-    constexpr int a = GroupTable<ELL>::mono_c(BETA, 0), b = GroupTable<ELL>::mono_c(BETA, 1);
-    constexpr int c = GroupTable<ELL>::mono_c(BETA, 2), d = GroupTable<ELL>::mono_c(BETA, 3);
-    if constexpr (d == 0) return f;
-    else if constexpr (d == -1) return nonzero_r ? f : 0.f;
-    else {
-      float v = f;
-#pragma unroll
-      for (int i = 0; i < a; ++i) v *= xh;
-#pragma unroll
-      for (int i = 0; i < b; ++i) v *= yh;
-#pragma unroll
-      for (int i = 0; i < c; ++i) v *= zh;
-      return v;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -183,6 +159,8 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restr
       const float Yc = rely[row0 + row];
       const float* frow = plane + (size_t)(row0 + row) * N;
       float2* lp = C + row * LL;
+      const float Ka = ipow_rt(X, aa) * ipow_rt(Yc, ab), Kb = ipow_rt(X, ba) * ipow_rt(Yc, bb);
+      const float xy2 = fmaf(X, X, Yc * Yc);
 #pragma unroll 1
       for (int q = 0; q < E / R0; ++q) {
         float2 v[R0];
@@ -191,12 +169,9 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restr
           const int z = fft_in_index<N>(tl, q, r);
           const float Zc = relz[z];
           const float f = frow[z];
-          const float r2 = fmaf(X, X, fmaf(Yc, Yc, Zc * Zc));
-          const bool nz = r2 > 0.f;
-          const float rinv = nz ? rsqrtf(r2) : 0.f;
-          const float xh = X * rinv, yh = Yc * rinv, zh = Zc * rinv;
-          v[r] = make_float2(basis_value_rt(f, xh, yh, zh, nz, aa, ab, ac, ad),
-                             basis_value_rt(f, xh, yh, zh, nz, ba, bb, bc, bd));
+          const float r2 = fmaf(Zc, Zc, xy2);
+          const float i2 = r2 > 0.f ? __frcp_rn(r2) : 0.f;
+          v[r] = make_float2(basis_value_rt(f, i2, Zc, Ka, ac, ad), basis_value_rt(f, i2, Zc, Kb, bc, bd));
         }
         Dft<R0>::run(v);
         const int jq = tl + q * TPL;
