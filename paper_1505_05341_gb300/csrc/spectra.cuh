@@ -131,7 +131,8 @@ struct YZ {
   static constexpr int LL = fft_line_len<N, true>();         // padded line length
   static constexpr size_t smem_z = sizeof(float2) * 2 * R * LL;
   static constexpr size_t smem_y = sizeof(float2) * NB * LL;
-  static constexpr size_t smem = sizeof(float2) * N + (smem_z > smem_y ? smem_z : smem_y);
+  static constexpr size_t smem_nodes = sizeof(float2) * R * N;  // (F, 1/|r|^2) per node of a row item
+  static constexpr size_t smem = sizeof(float2) * N + smem_nodes + (smem_z > smem_y ? smem_z : smem_y);
   static_assert(N % R == 0, "rows per item must divide N");
 };
 
@@ -142,7 +143,7 @@ struct YZ {
 // written to the ring slot.  C is one of two line buffers, so the split of this pair
 // can overlap the FFT of the next.
 template <int N, int ELL>
-__device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restrict__ plane, float X,
+__device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes, float X,
                                          const float* __restrict__ rely, const float* __restrict__ relz, int row0,
                                          const float2* tw, float2* __restrict__ zslot, int nzc) {
   using Y = YZ<N, ELL>;
@@ -157,10 +158,9 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restr
     const int row = ps * LPP + threadIdx.x / TPL;
     if (row < R) {
       const float Yc = rely[row0 + row];
-      const float* frow = plane + (size_t)(row0 + row) * N;
+      const float2* nrow = nodes + row * N;
       float2* lp = C + row * LL;
       const float Ka = ipow_rt(X, aa) * ipow_rt(Yc, ab), Kb = ipow_rt(X, ba) * ipow_rt(Yc, bb);
-      const float xy2 = fmaf(X, X, Yc * Yc);
 #pragma unroll 1
       for (int q = 0; q < E / R0; ++q) {
         float2 v[R0];
@@ -168,10 +168,8 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restr
         for (int r = 0; r < R0; ++r) {
           const int z = fft_in_index<N>(tl, q, r);
           const float Zc = relz[z];
-          const float f = frow[z];
-          const float r2 = fmaf(Zc, Zc, xy2);
-          const float i2 = r2 > 0.f ? __frcp_rn(r2) : 0.f;
-          v[r] = make_float2(basis_value_rt(f, i2, Zc, Ka, ac, ad), basis_value_rt(f, i2, Zc, Kb, bc, bd));
+          const float2 fi = nrow[z];  // written by this thread in row_item
+          v[r] = make_float2(basis_value_rt(fi.x, fi.y, Zc, Ka, ac, ad), basis_value_rt(fi.x, fi.y, Zc, Kb, bc, bd));
         }
         Dft<R0>::run(v);
         const int jq = tl + q * TPL;
@@ -194,15 +192,38 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float* __restr
   }
 }
 
+// Row item: the mesh value F and 1/|r|^2 of every node of the R rows are formed once
+// (each thread for the nodes it later reads, so no barrier is needed), then every
+// pair of basis fields is built from them, transformed along z and split.
 template <int N, int ELL>
-__device__ __forceinline__ void row_item(float2* work, const float* __restrict__ plane, float X,
+__device__ __forceinline__ void row_item(float2* work, float2* nodes, const float* __restrict__ plane, float X,
                                          const float* __restrict__ rely, const float* __restrict__ relz, int row0,
                                          const float2* tw, float2* __restrict__ zslot, int nzc) {
   using Y = YZ<N, ELL>;
-  constexpr int R = Y::R, LL = Y::LL;
+  constexpr int R = Y::R, LL = Y::LL, E = Y::E, TPL = Y::TPL, R0 = Y::R0, LPP = Y::LPP;
+  const int tl = threadIdx.x % TPL;
+#pragma unroll
+  for (int ps = 0; ps < Y::PASSES; ++ps) {
+    const int row = ps * LPP + threadIdx.x / TPL;
+    if (row < R) {
+      const float Yc = rely[row0 + row];
+      const float xy2 = fmaf(X, X, Yc * Yc);
+      const float* frow = plane + (size_t)(row0 + row) * N;
+      float2* nrow = nodes + row * N;
+#pragma unroll
+      for (int q = 0; q < E / R0; ++q)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int z = fft_in_index<N>(tl, q, r);
+          const float Zc = relz[z];
+          const float r2 = fmaf(Zc, Zc, xy2);
+          nrow[z] = make_float2(frow[z], r2 > 0.f ? __frcp_rn(r2) : 0.f);
+        }
+    }
+  }
 #pragma unroll 1
   for (int pr = 0; pr < Y::NPAIR; ++pr)
-    row_pair<N, ELL>(pr, work + (pr & 1) * R * LL, plane, X, rely, relz, row0, tw, zslot, nzc);
+    row_pair<N, ELL>(pr, work + (pr & 1) * R * LL, nodes, X, rely, relz, row0, tw, zslot, nzc);
 }
 
 template <int N, int ELL>
@@ -268,7 +289,8 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(
   __shared__ int s_item;
   __shared__ int s_ok;
   float2* tw = reinterpret_cast<float2*>(smem_raw);
-  float2* work = tw + N;
+  float2* nodes = tw + N;
+  float2* work = nodes + (Y::smem_nodes / sizeof(float2));
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = prm.tw[k];
   const int NZ = N / R, NY = prm.nzc, IPS = NZ + NY;
   const int mN = prm.m * N;
@@ -293,8 +315,8 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(
         if (!s_ok) break;
         const int j = p / N, ix = p - j * N;
         const float* rel = prm.rel + (size_t)j * 3 * N;
-        row_item<N, ELL>(work, prm.mesh + j * n3 + (size_t)ix * N * N, rel[ix], rel + N, rel + 2 * N, sub * R, tw,
-                         prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc);
+        row_item<N, ELL>(work, nodes, prm.mesh + j * n3 + (size_t)ix * N * N, rel[ix], rel + N, rel + 2 * N, sub * R,
+                         tw, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc);
         signal_release(prm.done_z + p);
       }
     } else {
