@@ -126,7 +126,7 @@ ys_status make_gmap(Plan& p) {
   const int P = x_pencils_for(p.n);
   const cuuint64_t dims[2] = {(cuuint64_t)2 * p.np_pad, (cuuint64_t)p.m * p.ng * p.n};
   const cuuint64_t strides[1] = {(cuuint64_t)2 * p.np_pad * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)(2 * P), (cuuint32_t)std::min(p.n, 256)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * P), (cuuint32_t)x_box_rows(p.n)};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(&p.gmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.d_g, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,

@@ -52,7 +52,7 @@ cudaError_t run_yz(Plan& p) {
   prm.m = p.m;
   prm.S = p.ring_slots;
   prm.D = p.ring_lead;
-  prm.spin_limit = 4000000;  // ~1 s of 128 ns sleeps, then the kernel reports a timeout
+  prm.spin_limit = 1000000000;  // 1 s, then the kernel reports a timeout
   if ((err = cudaFuncSetAttribute(k_yz<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem)))
     return err;
   LaunchScope ls(p, 4);

@@ -88,7 +88,7 @@ struct YZParams {
   int* ticket;           // [1]
   int* err;              // [1]
   int nzc, np, m, S, D;
-  long long spin_limit;
+  long long spin_limit;  // ns
 };
 
 template <int N>
@@ -102,14 +102,25 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 
 // Thread 0 waits until *addr >= target; false (and the error flag set) on timeout
 // or when another CTA has already failed.
-__device__ __forceinline__ bool wait_geq(const int* addr, int target, int* err, long long limit) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0 waits until *addr >= target, for at most limit_ns nanoseconds; false (and
+// the error flag set) on timeout, or when another CTA has already failed.
+__device__ __forceinline__ bool wait_geq(const int* addr, int target, int* err, long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
   long long it = 0;
   while (ld_acquire(addr) < target) {
-    if (++it > limit) {
-      atomicExch(err, 1);
-      return false;
+    if ((++it & 31) == 0) {
+      if (*reinterpret_cast<volatile int*>(err)) return false;
+      if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+        atomicExch(err, 1);
+        return false;
+      }
     }
-    if ((it & 31) == 0 && *reinterpret_cast<volatile int*>(err)) return false;
     __nanosleep(128);
   }
   return true;
@@ -167,7 +178,7 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int z = fft_in_index<N>(tl, q, r);
-          const float Zc = relz[z];
+          const float Zc = (ac | bc) ? relz[z] : 0.f;
           const float2 fi = nrow[z];  // written by this thread in row_item
           v[r] = make_float2(basis_value_rt(fi.x, fi.y, Zc, Ka, ac, ad), basis_value_rt(fi.x, fi.y, Zc, Kb, bc, bd));
         }
@@ -389,8 +400,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }
 
 // Bounded wait for the given phase parity of an mbarrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
-  for (long long it = 0; it < limit; ++it) {
+// Wait for an mbarrier phase for at most limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -398,8 +411,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((long long)(globaltimer_ns() - t0) > limit_ns) return false;
   }
-  return false;
 }
 
 template <int N, int ELL, int M>
@@ -411,8 +424,9 @@ struct XCombine {
   static constexpr int NW = THREADS / 32;
   static constexpr int NG = GroupTable<ELL>::NG;
   static constexpr int TILES = NG * M;
-  static constexpr int BOX_ROWS = N < 256 ? N : 256;
+  static constexpr int BOX_ROWS = x_box_rows(N);
   static constexpr int BOXES = N / BOX_ROWS;
+  static_assert(BOXES * BOX_ROWS == N, "boxes must tile the x axis");
   static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
   static_assert(THREADS % 32 == 0, "threads");
@@ -481,7 +495,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   float2 ph_pen = make_float2(1.f, 0.f);
   for (int s = 0; s < total; ++s) {
     if (tid == 0 && s + 1 < total) issue(s + 1);
-    if (!mbar_wait(&bar[s & 1], (s >> 1) & 1, 1LL << 24)) s_fail = 1;
+    if (!mbar_wait(&bar[s & 1], (s >> 1) & 1, 1000000000LL)) s_fail = 1;  // 1 s
     __syncthreads();
     if (s_fail) break;
     const int k = s / TILES, t = s - k * TILES;
@@ -564,7 +578,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
     if (tid == 0) {
       atomicExch(err, 2);
       // let any copy still in flight land before the CTA exits (bounded)
-      for (int b = 0; b < 2; ++b) mbar_wait(&bar[b], 0, 1LL << 20);
+      for (int b = 0; b < 2; ++b) mbar_wait(&bar[b], 0, 100000000LL);  // 0.1 s
     }
     return;
   }

@@ -117,6 +117,12 @@ void set_tiles(Plan& p, int tx, int ty, int tz);
 // y,z grid size; updates the ring lead D and slots S (S never exceeds the allocation).
 void set_yz_grid(Plan& p, int grid, int lead_pct = 0);
 constexpr int kRingLeadPctMax = 200;
+
+// Rows (x values) per TMA box of the x stage: a divisor of N no larger than the
+// 256-element limit of a box dimension (N = 384 -> 192).
+__host__ __device__ constexpr int x_box_rows(int n) {
+  return n <= 256 ? n : (n % 256 == 0 ? 256 : (n % 192 == 0 ? 192 : 128));
+}
 ys_status ensure_particles(Plan& p, int64_t total);
 extern thread_local std::string g_last_cuda_error;
 cudaError_t launch_measure(Plan& p);

@@ -1,0 +1,59 @@
+"""Parity at full size and at the largest meshes.
+
+- The 512^3 survey workload (1e7 galaxies + 5e7 randoms, TSC with interlacing, l <= 4,
+  shells to 0.4 h/Mpc) in the launch configuration the benchmark times (autotuned),
+  against the FP64 oracle's FFT estimator with all 22 fields, every shell.
+- 384^3, 768^3 and 1024^3 meshes with NGP on nodes and no window, where the FFT
+  estimator equals the galaxy direct sum: the oracle's galaxy sum is evaluated on the
+  modes below 0.06 h/Mpc, which are the same modes for any mesh whose Nyquist
+  frequency lies above that.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.binning import BinSpec
+from test_gpu_parity import TOL, compare, to_dev
+
+torch = pytest.importorskip("torch")
+ys = pytest.importorskip("paper_1505_05341_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def test_survey512_full_size_matches_oracle():
+    gal, ran, geo, st = synth.workload("shell512_tsc_il")
+    bins = BinSpec(0.0, 0.01, 40)
+    with ys.Plan(512, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, ell_max=4,
+                 k_min=0.0, dk=0.01, n_bins=40, max_particles=gal.n + ran.n,
+                 stream=torch.cuda.current_stream().cuda_stream) as plan:
+        dgal, dran = to_dev(gal), to_dev(ran)
+        tuning = plan.autotune(dgal, dran, reps=1)
+        plan.assign(dgal, dran)
+        res = plan.measure()
+    print("tuned", list(tuning.tile), tuning.yz_grid, tuning.ring_lead)
+    ref = oracle.fft_multipoles(gal, ran, geo, 512, bins, assign="tsc", interlace=True, ell_max=4)
+    compare(res, ref, 4, "survey512")
+    # Poisson points: after the shot noise P_0 is mostly noise, so also hold every shell
+    # of the raw monopole to the bar, and P_2, P_4 to it in units of the raw monopole
+    has = ref.n_modes > 0
+    raw_ref = ref.sum0[has] / ref.n_modes[has] / ref.norm.I
+    raw_gpu = res.p0[has] + res.shot_noise
+    assert np.max(np.abs(raw_gpu - raw_ref) / raw_ref) <= TOL
+    for l in (2, 4):
+        d = np.abs(getattr(res, f"p{l}")[has] - getattr(ref, f"p{l}")[has]) / raw_ref
+        assert d.max() <= TOL, (l, d.max())
+
+
+@pytest.mark.parametrize("n", [384, 768, 1024])
+def test_large_mesh_ngp_on_nodes_matches_galaxy_sum(n):
+    box_min = (-0.5 * n, -0.25 * n, 0.125 * n)   # H = 1: every node is exact in float32
+    gal, ran, geo = synth.on_node_catalog(n, box_min, float(n), 400, 2000, seed=n, observer=(3.0, -7.0, 5.0))
+    bins = BinSpec(0.0, 0.01, 6)
+    ref = oracle.sum_gal(gal, ran, geo, 32, bins)
+    with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign="ngp", compensate=False, ell_max=4,
+                 k_min=0.0, dk=0.01, n_bins=6, stream=torch.cuda.current_stream().cuda_stream) as plan:
+        plan.assign(to_dev(gal), to_dev(ran))
+        res = plan.measure()
+    compare(res, ref, 4, f"ngp_on_nodes_{n}")
