@@ -140,6 +140,31 @@ def alg_bytes(n_gal, n_ran, n, m, groups, n_pencils):
     return 16 * (n_gal + n_ran) + m * 8 * n ** 3 + m * groups * 16 * n * n_pencils
 
 
+# FP32 issue peak of the GB300 (derived, not measured): 152 SMs x 128 FP32 lanes x
+# 2 flops per FMA x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def fft_flops(cls, n, m, n_pencils, nzc, pairs=8, fields=16, groups=9):
+    """Nominal FFT flops per launch (5 L log2 L per complex line of length L) of the
+    two transform kernels: the y,z stage transforms m N^2 lines along z per field
+    pair and m N nzc lines along y per basis field; the x stage m G lines per kept
+    pencil."""
+    line = 5.0 * n * math.log2(n)
+    if cls == "yz_stage":
+        return line * (m * n * n * pairs + m * n * nzc * fields)
+    if cls == "x_combine":
+        return line * m * groups * n_pencils
+    return 0.0
+
+
+# DRAM bytes (read + write) per launch that ncu measured for the current build of
+# each kernel on the 512^3 survey workload (one-pass dram__bytes_{read,write}.sum
+# capture; profiles/dram_traffic_shell512_tsc_il.md).  Remove an entry when its
+# kernel changes.
+TRAFFIC = {"yz_stage": 8.59e9, "x_combine": 5.77e9, "tile_deposit": 2.88e9}
+
+
 def kernel_bytes(cls, n_gal, n_ran, n, m, groups, n_pencils, launches_per_step, batch_planes):
     """Algorithmic bytes per launch of one kernel class."""
     if cls == "particle_count":
@@ -305,7 +330,7 @@ def run_ours(args):
         e2e_s = float(t.item())
     res = plan.measure()
 
-    n_pencils = plan_pencils(plan)
+    n_pencils, nzc = plan_pencils(plan, with_nzc=True)
     m, groups = 2, 9
     steps_prof = 2
     per_cls = {k: (v[0] / steps_prof, v[1] / max(1, v[0])) for k, v in prof.items() if v[0] > 0}
@@ -315,7 +340,21 @@ def run_ours(args):
     avg_ms = per_cls[dom][1]
     peak, peak_src = _peaks()
     achieved = bytes_dom / (avg_ms / 1e3) / 1e9
+    flops_dom = fft_flops(dom, N_MESH, m, n_pencils, nzc)
     b_alg = alg_bytes(gal.n, ran.n, N_MESH, m, groups, n_pencils)
+    if flops_dom > 0:
+        # the transform kernels are bound by FP32 issue, not by HBM
+        tflops = flops_dom / (avg_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS, "traffic": TRAFFIC.get(dom),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "flops_per_launch": flops_dom, "avg_launch_ms": avg_ms,
+                    "hbm_view": {"alg_bytes_per_launch": bytes_dom, "achieved_GBps": achieved, "peak_GBps": peak,
+                                 "frac": achieved / peak, "peak_source": peak_src}}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": TRAFFIC.get(dom), "peak_source": peak_src,
+                    "alg_bytes_per_launch": bytes_dom, "avg_launch_ms": avg_ms}
     ms_step = ms / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -326,12 +365,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (0.96 GB catalogue, 1 GB meshes, 11 GB spectra)",
                    "parallelism": f"replicas{world}",
                    "tuned": {"tile": list(tuning.tile), "yz_grid": tuning.yz_grid, "ring_lead": tuning.ring_lead}},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                     "alg_bytes_per_launch": bytes_dom, "avg_launch_ms": avg_ms},
-        "step_roofline": {"alg_bytes": b_alg, "achieved_GBps": b_alg / (ms_step / 1e3) / 1e9,
-                          "frac": b_alg / (ms_step / 1e3) / 1e9 / peak},
-        "kernels": {k: {"launches_per_step": v[0], "avg_ms": v[1]} for k, v in per_cls.items()},
+        "roofline": roofline,
+        "step_roofline": {"bound": "hbm", "alg_bytes": b_alg, "achieved_GBps": b_alg / (ms_step / 1e3) / 1e9,
+                          "peak_GBps": peak, "frac": b_alg / (ms_step / 1e3) / 1e9 / peak, "peak_source": peak_src},
+        "kernels": {k: {"launches_per_step": v[0], "avg_ms": v[1], "dram_bytes_ncu": TRAFFIC.get(k)}
+                    for k, v in per_cls.items()},
         "clocks": clk.summary(),
         "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 20 * (gal.n + ran.n),
                 "d2h_bytes_per_step": 8 * (5 * n_bins + 5)},
@@ -509,7 +547,7 @@ def run_learned(steps, n_heldout=200):
             "trained": {k: meta[k] for k in ("train_seeds", "rows", "steps", "lr", "lr_final")}}
 
 
-def plan_pencils(plan):
+def plan_pencils(plan, with_nzc=False):
     """Number of (k_y, k_z) pencils the plan keeps: k_y^2 + k_z^2 < n2_hi, derived
     from the shell edges exactly as the library does (integer |m|^2 test)."""
     L = plan.cfg.box_len
@@ -528,7 +566,7 @@ def plan_pencils(plan):
             kymax += 1
         cnt += 2 * kymax + 1
         kz += 1
-    return cnt
+    return (cnt, kz) if with_nzc else cnt
 
 
 def main():

@@ -275,6 +275,16 @@ __device__ __forceinline__ void column_item(float2* S, const float2* __restrict_
     }
   }
   line_group_sync<TPL>();  // each line is written and read by its own threads
+  // The ring lines of this column are dead once read: drop them from L2 without a
+  // write-back (the slot is rewritten only after this item's completion is
+  // released).  Each line is N * 8 bytes, a whole number of 128-byte lines.
+  for (int base = 0; base < NB; base += LPP) {
+    const int f = base + threadIdx.x / TPL;
+    if (f < NB && tl < N / 16) {
+      const float2* line = zs + ((size_t)f * nzc + kz) * N;
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(line + tl * 16) : "memory");
+    }
+  }
   FftRun<N, 1, false, true, NB>::run(S, 1, LL, NB, tw);
   __syncthreads();
   column_fold<N, ELL>(S, kz, col_off, gout, j, ix, np);
