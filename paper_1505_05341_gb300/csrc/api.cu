@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "fft.cuh"
 #include "ys_internal.h"
 
 namespace ys {
@@ -204,8 +205,15 @@ ys_status build_tables(Plan& p) {
     if (m != 0) W = std::pow(std::sin(x) / x, pw);
     invw[i] = c.compensate ? (float)(1.0 / W) : 1.0f;
     phase[i] = make_float2((float)std::cos(x), (float)-std::sin(x));
-    const double t = -2.0 * M_PI * i / n;
-    tw[i] = make_float2((float)std::cos(t), (float)std::sin(t));
+  }
+  // stage-major twiddles (fft_tw_offset): exp(-2 pi i r k / (N_s R_s)) per stage
+  for (int st = 1; st < fft_nstages(n); ++st) {
+    const int ns = fft_ns_before(n, st), rad = fft_radix(n, st), off = fft_tw_offset(n, st);
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < rad; ++r) {
+        const double t = -2.0 * M_PI * r * k / ((double)ns * rad);
+        tw[off + k * (rad - 1) + r - 1] = make_float2((float)std::cos(t), (float)std::sin(t));
+      }
   }
   // node positions (hi, lo) for i in [-1, n + 1], and node - observer per mesh
   std::vector<float2> nodes(3 * (n + 3));

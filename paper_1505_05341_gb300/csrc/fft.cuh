@@ -1,12 +1,12 @@
 // Shared-memory complex FFTs for the mesh transforms (forward, e^{-2 pi i j k / N}).
 //
-// The paper (Sec. 3) only needs "any FFT algorithm"; this one is a Stockham
-// autosort decimation-in-time transform with the result in natural order.  N is
-// 2^a (radix-8 stages, then one radix-4 or radix-2) or 3 * 2^a (radix-4 stages, an
-// optional radix-2, then radix-3).  Each thread holds E = 8 (or 12) elements per line
-// and does E / R butterflies per stage; the data go through shared memory between
-// stages.  Twiddles come from a table tw[j] = exp(-2 pi i j / N) computed in FP64 on
-// the host and rounded to float.
+// The method (Sec. 3) places no condition on the FFT algorithm; this one is a
+// Stockham autosort decimation-in-time transform with the result in natural order.
+// N is 2^a (radix-8 stages, then one radix-4 or radix-2) or 3 * 2^a (radix-4 stages,
+// an optional radix-2, then radix-3).  Each thread holds E = 8 (or 12) elements per
+// line and does E / R butterflies per stage; the data go through shared memory
+// between stages.  Twiddles come from a stage-major table (fft_tw_offset) computed
+// in FP64 on the host and rounded to float.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -140,12 +140,28 @@ __host__ __device__ constexpr int fft_pos(int i) { return PAD ? i + (i >> 3) : i
 template <int N, bool PAD>
 __host__ __device__ constexpr int fft_line_len() { return PAD ? N + N / 8 + 1 : N + 1; }
 
+// Twiddles are stored stage by stage: for stage s >= 1 (N_s = fft_ns_before(N, s)
+// elements already combined, radix R_s), entry k (R_s - 1) + r - 1 of the stage's
+// block is exp(-2 pi i r k / (N_s R_s)), k < N_s, 1 <= r < R_s.  A butterfly then
+// reads its R_s - 1 twiddles from one base address.  The blocks fill N - R_0 < N
+// entries in all.
+__host__ __device__ constexpr int fft_tw_offset(int n, int stage) {
+  int off = 0;
+  for (int s = 1; s < stage; ++s) off += fft_ns_before(n, s) * (fft_radix(n, s) - 1);
+  return off;
+}
+
 // One Stockham stage over `nl` lines of length N stored in shared memory at
 // buf[line * ls + elem * es].  LF: consecutive threads take consecutive lines (for
 // layouts whose lines interleave); otherwise consecutive threads walk one line.
 // NL > 0: the number of lines is a compile-time constant (passes unrolled, separated
 // by a line-group barrier so that no pass's addresses are hoisted into another);
 // NL == 0: nl lines at run time.
+//
+// Padded lines walked by consecutive threads (the y,z stage) take a fast path when the
+// threads per line, the input stride and N_s are multiples of 8: element i sits at
+// i + i/8, and (a + 8 m)/8 = a/8 + m, so every load and store is one per-thread base
+// address plus a compile-time offset.
 template <int N, int S, bool LF, bool PAD, int NL = 0>
 __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt, const float2* tw) {
   constexpr int R = fft_radix(N, S);
@@ -154,7 +170,8 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
   constexpr int NB = E / R;         // butterflies per thread
   constexpr int NS = fft_ns_before(N, S);
   constexpr int STRIDE = N / R;
-  constexpr int TWS = N / (NS * R);
+  constexpr bool FAST = !LF && PAD && TPL % 8 == 0 && STRIDE % 8 == 0 && NS % 8 == 0;
+  const float2* tws = tw + fft_tw_offset(N, S);
   // Lines walked by consecutive threads only need their own threads synchronised.
   const int tid = threadIdx.x;
   const int lpp = blockDim.x / TPL;  // lines per pass
@@ -168,29 +185,44 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
     const bool ok = in_pass && line < nl;
     float2 v[E];
     if (ok) {
-      float2* lp = buf + (size_t)line * ls;
+      const float2* lp = buf + line * ls;
+      if constexpr (FAST) {
+        const float2* src = lp + (tl + (tl >> 3));
 #pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        const int j = tl + q * TPL;
+        for (int q = 0; q < NB; ++q)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q * R + r] = lp[fft_pos<PAD>(j + r * STRIDE) * es];
+          for (int r = 0; r < R; ++r) v[q * R + r] = src[(q * TPL + r * STRIDE) / 8 * 9];
+      } else {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int j = tl + q * TPL;
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = lp[fft_pos<PAD>(j + r * STRIDE) * es];
+        }
       }
     }
     if constexpr (LF) __syncthreads(); else line_group_sync<TPL>();
     if (ok) {
-      float2* lp = buf + (size_t)line * ls;
+      float2* lp = buf + line * ls;
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
         const int j = tl + q * TPL;
         const int k = j % NS;
         if (NS > 1) {
+          const float2* tk = tws + k * (R - 1);
 #pragma unroll
-          for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tw[r * k * TWS]);
+          for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tk[r - 1]);
         }
         Dft<R>::run(&v[q * R]);
         const int outb = (j / NS) * NS * R + k;
+        if constexpr (FAST) {
+          float2* dst = lp + (outb + (outb >> 3));
 #pragma unroll
-        for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(outb + r * NS) * es] = v[q * R + r];
+          for (int r = 0; r < R; ++r) dst[r * NS / 8 * 9] = v[q * R + r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(outb + r * NS) * es] = v[q * R + r];
+        }
       }
     }
     if constexpr (LF) __syncthreads(); else line_group_sync<TPL>();
@@ -223,7 +255,7 @@ __device__ __forceinline__ void fft_last_stage_regs(const float2* lp, int es, in
   constexpr int NB = E / R;
   constexpr int NS = fft_ns_before(N, S);
   constexpr int STRIDE = N / R;
-  constexpr int TWS = N / (NS * R);
+  const float2* tws = tw + fft_tw_offset(N, S);
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int j = tl + q * TPL;
@@ -235,8 +267,9 @@ __device__ __forceinline__ void fft_last_stage_regs(const float2* lp, int es, in
     const int j = tl + q * TPL;
     const int k = j % NS;
     if (NS > 1) {
+      const float2* tk = tws + k * (R - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tw[r * k * TWS]);
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tk[r - 1]);
     }
     Dft<R>::run(&v[q * R]);
   }
@@ -245,7 +278,7 @@ __device__ __forceinline__ void fft_last_stage_regs(const float2* lp, int es, in
 // First stage from registers: the caller holds, for its butterflies q < E/R0, the
 // inputs v[q * R0 + r] = x[fft_in_index<N>(tl, q, r)] of one line; this does the
 // stage-0 butterflies (no twiddles: N_s = 1) and stores the results to the line lp.
-// The remaining stages run with FftRun<N, 1, LF> after a __syncthreads().
+// The remaining stages run with FftRun<N, 1, LF> after a line-group barrier.
 template <int N>
 __host__ __device__ constexpr int fft_in_index(int tl, int q, int r) {
   return tl + q * (N / fft_elems(N)) + r * (N / fft_radix(N, 0));
@@ -260,8 +293,14 @@ __device__ __forceinline__ void fft_stage0_regs(float2 (&v)[fft_elems(N)], float
   for (int q = 0; q < E / R; ++q) {
     Dft<R>::run(&v[q * R]);
     const int j = tl + q * TPL;
+    if constexpr (PAD && R == 8) {
+      float2* dst = lp + 9 * j * es;  // element 8 j + r sits at 9 j + r
 #pragma unroll
-    for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(j * R + r) * es] = v[q * R + r];
+      for (int r = 0; r < R; ++r) dst[r * es] = v[q * R + r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(j * R + r) * es] = v[q * R + r];
+    }
   }
 }
 

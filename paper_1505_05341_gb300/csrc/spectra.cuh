@@ -184,8 +184,14 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
         }
         Dft<R0>::run(v);
         const int jq = tl + q * TPL;
+        if constexpr (R0 == 8) {
+          float2* dst = lp + 9 * jq;  // element 8 jq + r sits at 9 jq + r
 #pragma unroll
-        for (int r = 0; r < R0; ++r) lp[fft_pos<true>(jq * R0 + r)] = v[r];
+          for (int r = 0; r < R0; ++r) dst[r] = v[r];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R0; ++r) lp[fft_pos<true>(jq * R0 + r)] = v[r];
+        }
       }
     }
   }

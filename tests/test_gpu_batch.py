@@ -1,12 +1,14 @@
 """Batched runs (one graph launch over catalogues of mixed size and mesh) and the
-autotuner: every row equals the same catalogue run alone, within the parity bar,
-and the oracle; replaying the captured graph reproduces the rows."""
+autotuner: every row, in the first run and in a replay of the captured graph,
+meets the parity bar against the FP64 oracle, and agrees with the same catalogue
+run alone to within twice that bar."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
 from oracle.binning import BinSpec
+from test_gpu_parity import compare
 
 torch = pytest.importorskip("torch")
 ys = pytest.importorskip("paper_1505_05341_gb300")
@@ -20,7 +22,7 @@ def dev(c):
     return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (c.x, c.y, c.z, c.w, c.nbar))
 
 
-def close_rows(a, b, label):
+def close_rows(a, b, label, tol):
     np.testing.assert_array_equal(a.n_modes, b.n_modes)
     has = a.n_modes > 0
     raw = a.p0 + a.shot_noise
@@ -28,7 +30,7 @@ def close_rows(a, b, label):
         x, y = getattr(a, f"p{l}"), getattr(b, f"p{l}")
         sel = has & (np.abs(x) > 1e-2 * np.abs(raw))
         if sel.any():
-            assert np.max(np.abs(y[sel] - x[sel]) / np.abs(x[sel])) <= TOL, (label, l)
+            assert np.max(np.abs(y[sel] - x[sel]) / np.abs(x[sel])) <= tol, (label, l)
 
 
 def batch_inputs():
@@ -63,19 +65,16 @@ def test_batch_rows_equal_single_runs_and_oracle():
         with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign=kind, interlace=il, dk=0.01) as plan:
             plan.assign(gals[i], rans[i])
             single = plan.measure()
-        assert rows[i].status == 0
-        close_rows(single, rows[i], f"batch row {i}")
-        close_rows(single, rows2[i], f"replayed row {i}")
-    gal, ran, geo, n, kind, il = cats[2]
-    bins = BinSpec.up_to(np.pi * n / geo.box_len, 0.01)
-    ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign=kind, interlace=il)
-    np.testing.assert_array_equal(rows[2].n_modes, ref.n_modes)
-    has = ref.n_modes > 0
-    raw = ref.sum0[has] / ref.n_modes[has] / ref.norm.I
-    for l in (0, 2, 4):
-        g, o = getattr(rows[2], f"p{l}")[has], getattr(ref, f"p{l}")[has]
-        sel = np.abs(o) > 1e-2 * raw
-        assert np.max(np.abs(g[sel] - o[sel]) / np.abs(o[sel])) <= TOL
+        assert rows[i].status == 0 and rows2[i].status == 0
+        # every row, first run and replay, against the FP64 oracle at the parity bar
+        bins = BinSpec.up_to(np.pi * n / geo.box_len, 0.01)
+        ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign=kind, interlace=il)
+        compare(rows[i], ref, 4, f"batch row {i}")
+        compare(rows2[i], ref, 4, f"replayed row {i}")
+        # two float32 evaluations that each meet the bar differ by at most twice it
+        # (the deposit's shared-memory atomics add in a different order per run)
+        close_rows(single, rows[i], f"batch row {i} vs single", 2 * TOL)
+        close_rows(single, rows2[i], f"replayed row {i} vs single", 2 * TOL)
 
 
 def test_autotune_keeps_results():
@@ -85,9 +84,10 @@ def test_autotune_keeps_results():
         plan.assign(g, r)
         before = plan.measure()
         t = plan.autotune(g, r, reps=2)
-        assert all(v > 0 for v in t.tile) and t.yz_grid > 0 and t.measure_ms > 0
+        assert all(v > 0 for v in t.tile) and t.yz_grid > 0 and t.ring_lead > 0 and t.measure_ms > 0
         after_tune = plan.measure()
         plan.assign(g, r)
         after = plan.measure()
-    close_rows(before, after_tune, "autotune state")
-    close_rows(before, after, "after autotune")
+    # other tiles and grids add the same terms in another order: twice the parity bar
+    close_rows(before, after_tune, "autotune state", 2 * TOL)
+    close_rows(before, after, "after autotune", 2 * TOL)
