@@ -198,14 +198,22 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
   line_group_sync<TPL>();  // each line is written and read by its own threads
   FftRun<N, 1, false, true, R>::run(C, 1, LL, R, tw);
   __syncthreads();
-  for (int e = threadIdx.x; e < nzc * R; e += blockDim.x) {
-    const int kz = e / R, r = e - kz * R;
-    const float2 ck = C[r * LL + fft_pos<true>(kz)];
-    const float2 cm = C[r * LL + fft_pos<true>(kz == 0 ? 0 : N - kz)];
+  // Split: thread t takes row r = t mod R and k_z = t / R + i KS.  KS is a multiple
+  // of 8, so the padded positions of k_z and N - k_z move by fixed steps.
+  static_assert(Y::THREADS % R == 0 && (Y::THREADS / R) % 8 == 0, "split stride");
+  constexpr int KS = Y::THREADS / R, PSTEP = KS / 8 * 9;
+  const int r = threadIdx.x % R, kz0 = threadIdx.x / R;
+  const float2* crow = C + r * LL;
+  const float2* pk = crow + fft_pos<true>(kz0);
+  const float2* pm = crow + fft_pos<true>(N - kz0);  // only read for k_z > 0
+  float2* za = zslot + ((size_t)fa * nzc + kz0) * N + row0 + r;
+  const size_t fstep = (size_t)nzc * N;
+  for (int kz = kz0; kz < nzc; kz += KS, pk += PSTEP, pm -= PSTEP, za += (size_t)KS * N) {
+    const float2 ck = *pk;
+    const float2 cm = kz ? *pm : ck;
     // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i).
-    zslot[((size_t)fa * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
-    if (fb < NB)
-      zslot[((size_t)fb * nzc + kz) * N + row0 + r] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
+    za[0] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
+    if (fb < NB) za[fstep] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
   }
 }
 
@@ -251,13 +259,16 @@ __device__ __forceinline__ void column_fold(const float2* S, int kz, const int* 
   const int p0 = col_off[kz];
   const int cnt = col_off[kz + 1] - p0;
   const int kymax = (cnt - 1) / 2;
+  const size_t gstep = (size_t)N * np;  // between groups
+  float2* g0 = gout + ((size_t)j * NG * N + ix) * np + p0;
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
     const int ky = q - kymax;
-    const int pos = fft_pos<true>(ky < 0 ? ky + N : ky);
+    const float2* sp = S + fft_pos<true>(ky < 0 ? ky + N : ky);
     float2 g[NG];
-    GroupTable<ELL>::combine([&](int f) { return S[f * LL + pos]; }, (float)ky, (float)kz, g);
+    GroupTable<ELL>::combine([&](int f) { return sp[f * LL]; }, (float)ky, (float)kz, g);
+    float2* gp = g0 + q;
 #pragma unroll
-    for (int gi = 0; gi < NG; ++gi) gout[(((size_t)j * NG + gi) * N + ix) * np + p0 + q] = g[gi];
+    for (int gi = 0; gi < NG; ++gi) gp[gi * gstep] = g[gi];
   }
 }
 
