@@ -66,10 +66,17 @@ __host__ __device__ constexpr int fft_ns_before(int n, int stage) {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// -i * a
-__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+// Complex sums and differences use the packed two-lane float instructions of
+// sm_100-class GPUs (one instruction for both components).  a - b is formed as
+// fma(b, -1, a), whose product is exact, so it rounds exactly as a - b does.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 cswap(float2 a) { return make_float2(a.y, a.x); }
+// a + (-i) t and a - (-i) t
+__device__ __forceinline__ float2 add_mi(float2 a, float2 t) { return __ffma2_rn(cswap(t), make_float2(1.f, -1.f), a); }
+__device__ __forceinline__ float2 sub_mi(float2 a, float2 t) { return __ffma2_rn(cswap(t), make_float2(-1.f, 1.f), a); }
+// a + s t for a real s given as (s, s)
+__device__ __forceinline__ float2 cfma(float2 t, float2 s, float2 a) { return __ffma2_rn(t, s, a); }
 
 template <int R> struct Dft;
 
@@ -87,12 +94,12 @@ template <> struct Dft<3> {
     const float s3 = 0.866025403784438647f;
     const float2 a = v[0], b = v[1], c = v[2];
     const float2 t1 = cadd(b, c);
-    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
+    const float2 t2 = cfma(t1, make_float2(-0.5f, -0.5f), a);
     const float2 d = csub(b, c);
-    const float2 t3 = make_float2(s3 * d.y, -s3 * d.x);  // -i sqrt3/2 (b - c)
+    // t2 +/- (-i sqrt3/2) d
     v[0] = cadd(a, t1);
-    v[1] = cadd(t2, t3);
-    v[2] = csub(t2, t3);
+    v[1] = cfma(cswap(d), make_float2(s3, -s3), t2);
+    v[2] = cfma(cswap(d), make_float2(-s3, s3), t2);
   }
 };
 
@@ -100,11 +107,11 @@ template <> struct Dft<4> {
   __device__ static __forceinline__ void run(float2* v) {
     const float2 a = v[0], b = v[1], c = v[2], d = v[3];
     const float2 s0 = cadd(a, c), s1 = csub(a, c);
-    const float2 s2 = cadd(b, d), s3 = cmul_mi(csub(b, d));
+    const float2 s2 = cadd(b, d), t = csub(b, d);
     v[0] = cadd(s0, s2);
     v[2] = csub(s0, s2);
-    v[1] = cadd(s1, s3);
-    v[3] = csub(s1, s3);
+    v[1] = add_mi(s1, t);
+    v[3] = sub_mi(s1, t);
   }
 };
 
@@ -116,17 +123,18 @@ template <> struct Dft<8> {
     float2 o[4] = {v[1], v[3], v[5], v[7]};
     Dft<4>::run(e);
     Dft<4>::run(o);
-    const float2 o1 = make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));   // (1-i)/sqrt2
-    const float2 o2 = cmul_mi(o[2]);                                              // -i
-    const float2 o3 = make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));  // (-1-i)/sqrt2
+    // w8 o1 = h u1 with u1 = (o1.x + o1.y, o1.y - o1.x); w8^3 o3 = -h u3 with
+    // u3 = (o3.x - o3.y, o3.y + o3.x); w8^2 o2 = -i o2.
+    const float2 u1 = add_mi(o[1], o[1]);
+    const float2 u3 = sub_mi(o[3], o[3]);
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], o1);
-    v[5] = csub(e[1], o1);
-    v[2] = cadd(e[2], o2);
-    v[6] = csub(e[2], o2);
-    v[3] = cadd(e[3], o3);
-    v[7] = csub(e[3], o3);
+    v[1] = cfma(u1, make_float2(h, h), e[1]);
+    v[5] = cfma(u1, make_float2(-h, -h), e[1]);
+    v[2] = add_mi(e[2], o[2]);
+    v[6] = sub_mi(e[2], o[2]);
+    v[3] = cfma(u3, make_float2(-h, -h), e[3]);
+    v[7] = cfma(u3, make_float2(h, h), e[3]);
   }
 };
 
