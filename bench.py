@@ -227,7 +227,7 @@ def run_reference(args):
     sample = ""
     cores = _cores()
     for i in range(args.warmup + args.steps):
-        per_cat, sample, cores = cpu_sample(gal, ran, geo, frac=0.02, n_fields=1)
+        per_cat, sample, cores = cpu_sample(gal, ran, geo, frac=0.02, n_fields=7)
         if i >= args.warmup:
             times.append(per_cat)
     value = 1.0 / statistics.mean(times)
