@@ -177,10 +177,10 @@ ys_status ys_plan_get_stats(ys_plan* plan, ys_stats* out, int reset);
  * Inputs: gal, ran with DEVICE pointers, as for ys_assign.  Output: the plan's mesh(es)
  * and catalogue sums, consumed by the next ys_measure_multipoles*.  Asynchronous on
  * the plan's stream.
- * Limits: the records need (gal->n + ran->n) * T * 20 bytes, T = 2^(axes with more
+ * Limits: the records need (gal->n + ran->n) * T * 16 bytes, T = 2^(axes with more
  * than one 16/16/32-node tile) <= 8, plus 12 bytes per tile; a catalogue that does
  * not fit returns YS_ERR_UNSUPPORTED before any work is queued (ys_last_cuda_error()
- * then gives the sizes).  For a 256^3 mesh (T = 8) this is about 400 000 particles.
+ * then gives the sizes).  For a 256^3 mesh (T = 8) this is about 520 000 particles.
  * Set-up: the first call on each device looks up the array's device address with
  * cudaGetSymbolAddress while that device is current; make that first call before
  * any stream capture.

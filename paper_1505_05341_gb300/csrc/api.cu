@@ -56,7 +56,7 @@ void free_all(Plan& p) {
   dfree(p.d_tw); dfree(p.d_nodes); dfree(p.d_rel); dfree(p.d_invw); dfree(p.d_phase);
   dfree(p.d_col_off); dfree(p.d_pencil); dfree(p.d_lut); dfree(p.d_shell);
   dfree(p.d_mesh); dfree(p.d_z); dfree(p.d_sync); dfree(p.d_g); dfree(p.d_acc); dfree(p.d_sums); dfree(p.d_result);
-  dfree(p.d_tile_count); dfree(p.d_tile_off); dfree(p.d_tile_cur); dfree(p.d_rec); dfree(p.d_rec_cell);
+  dfree(p.d_tile_count); dfree(p.d_tile_off); dfree(p.d_tile_cur); dfree(p.d_rec);
   dfree(p.d_stage);
   p.device_bytes = 0;
 }
@@ -264,9 +264,8 @@ ys_status ensure_particles(Plan& p, int64_t total) {
   cudaError_t e;
   if (p.d_rec) {
     if ((e = cudaStreamSynchronize(p.stream))) return cuda_fail(e);
-    p.device_bytes -= (size_t)p.rec_cap * (sizeof(float4) + sizeof(int)) + 32;
+    p.device_bytes -= (size_t)p.rec_cap * sizeof(float4) + 16;
     dfree(p.d_rec);
-    dfree(p.d_rec_cell);
   }
   // records per particle: up to 2 tiles per axis that has more than one tile, for
   // any scatter-tile shape the tuner may switch to
@@ -279,7 +278,6 @@ ys_status ensure_particles(Plan& p, int64_t total) {
   p.part_cap = total;
   p.rec_cap = total * factor;
   if ((e = dalloc(p, p.d_rec, (size_t)p.rec_cap))) return cuda_fail(e);
-  if ((e = dalloc(p, p.d_rec_cell, (size_t)p.rec_cap))) return cuda_fail(e);
   return YS_OK;
 }
 

@@ -13,7 +13,9 @@
 //
 //   k_count   : cell index per particle, FP64-accumulated sums, per-tile counts
 //   k_scan    : exclusive scan of the counts (one CTA)
-//   k_bin     : records (sub-cell offsets, signed weight, packed cell) per tile
+//   k_bin     : one 16-byte record (position, signed weight) per tile touched
+//               (the deposit locates the particle again: 20-byte records with the
+//               cell index cost two partial L2 sector writes each)
 //   k_deposit : per-tile shared-memory deposit and store
 //
 // Sub-cell offsets are formed against a host-built FP64 table of node positions
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(THREADS)
 k_particles(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
             const float* __restrict__ pw, const float* __restrict__ pnbar, int64_t n, int is_ran,
             Geom g, const float2* __restrict__ nodes, unsigned* __restrict__ tile_count,
-            unsigned* __restrict__ tile_cur, float4* __restrict__ rec, int* __restrict__ rec_cell,
+            unsigned* __restrict__ tile_cur, float4* __restrict__ rec,
             double* __restrict__ sums, double alpha_cfg) {
   // Compensated float sums per thread (Kahan), FP64 across threads.
   float s_w = 0.f, c_w = 0.f, s_w2 = 0.f, c_w2 = 0.f, s_w2n = 0.f, c_w2n = 0.f;
@@ -176,7 +178,6 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
       }
     }
     const float weff = w * wscale;
-    const int packed = (ci[0] << 20) | (ci[1] << 10) | ci[2];
     for (int a = 0; a < nt[0]; ++a)
       for (int b = 0; b < nt[1]; ++b)
         for (int c = 0; c < nt[2]; ++c) {
@@ -185,8 +186,7 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
             atomicAdd(&tile_count[tile], 1u);
           } else {
             const unsigned slot = atomicAdd(&tile_cur[tile], 1u);
-            rec[slot] = make_float4(cd[0], cd[1], cd[2], weff);
-            rec_cell[slot] = packed;
+            rec[slot] = make_float4(x, y, z, weff);
           }
         }
   }
@@ -243,8 +243,8 @@ k_scan(const unsigned* __restrict__ count, int ntiles, unsigned* __restrict__ of
 
 template <int KIND, int M>
 __global__ void __launch_bounds__(THREADS)
-k_deposit(Geom g, const unsigned* __restrict__ off, const float4* __restrict__ rec,
-          const int* __restrict__ rec_cell, float* __restrict__ mesh) {
+k_deposit(Geom g, const float2* __restrict__ nodes, const unsigned* __restrict__ off,
+          const float4* __restrict__ rec, float* __restrict__ mesh) {
   extern __shared__ float s_tile[];
   const int n = g.n;
   const int tdx = g.tdim[0], tdy = g.tdim[1], tdz = g.tdim[2];
@@ -260,9 +260,11 @@ k_deposit(Geom g, const unsigned* __restrict__ off, const float4* __restrict__ r
   const unsigned b = off[tile], e = off[tile + 1];
   for (unsigned r = b + threadIdx.x; r < e; r += blockDim.x) {
     const float4 q = rec[r];
-    const int packed = rec_cell[r];
-    const int ci[3] = {(packed >> 20) & 1023, (packed >> 10) & 1023, packed & 1023};
-    const float cd[3] = {q.x, q.y, q.z};
+    int ci[3];
+    float cd[3];  // the cell and offset the binning pass found (same arithmetic)
+    locate(q.x, 0, g, nodes, ci[0], cd[0]);
+    locate(q.y, 1, g, nodes, ci[1], cd[1]);
+    locate(q.z, 2, g, nodes, ci[2], cd[2]);
 #pragma unroll
     for (int mj = 0; mj < M; ++mj) {
       int loc[3][3];
@@ -320,7 +322,7 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
     if (k.n == 0) continue;
     LaunchScope ls(p, 0);
     k_particles<KIND, M, false><<<blocks(k.n), THREADS, 0, st>>>(
-        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr, nullptr,
+        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr,
         p.d_sums, p.cfg.alpha);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -334,7 +336,7 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
     if (k.n == 0) continue;
     LaunchScope ls(p, 2);
     k_particles<KIND, M, true><<<blocks(k.n), THREADS, 0, st>>>(
-        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, nullptr, p.d_tile_cur, p.d_rec, p.d_rec_cell,
+        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, nullptr, p.d_tile_cur, p.d_rec,
         p.d_sums, p.cfg.alpha);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -344,7 +346,7 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
       cudaSuccess)
     return err;
   LaunchScope ls(p, 3);
-  k_deposit<KIND, M><<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_tile_off, p.d_rec, p.d_rec_cell, p.d_mesh);
+  k_deposit<KIND, M><<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_nodes, p.d_tile_off, p.d_rec, p.d_mesh);
   return cudaGetLastError();
 }
 

@@ -55,12 +55,11 @@ ys_status assign_noalloc(Plan& p, const ys_catalog& gal, const ys_catalog& ran, 
   for (int a = 0; a < 3; ++a) factor *= p.geom.tiles[a] > 1 ? 2 : 1;
   const size_t nt = (size_t)p.ntiles;
   const size_t records = (size_t)(gal.n + ran.n) * factor;
-  // Layout: tile counts | tile offsets | tile cursors | records (float4) | cells (int)
+  // Layout: tile counts | tile offsets | tile cursors | records (float4)
   const size_t off_off = align256(nt * sizeof(unsigned));
   const size_t off_cur = off_off + align256((nt + 1) * sizeof(unsigned));
   const size_t off_rec = off_cur + align256(nt * sizeof(unsigned));
-  const size_t off_cell = off_rec + align256(records * sizeof(float4));
-  const size_t need = off_cell + records * sizeof(int);
+  const size_t need = off_rec + records * sizeof(float4);
   if (need > NOALLOC_BYTES) {
     why = "catalogue too large for the no-allocation scratch: " + std::to_string(gal.n + ran.n) +
           " particles need " + std::to_string(need) + " bytes (up to " + std::to_string(factor) +
@@ -80,18 +79,15 @@ ys_status assign_noalloc(Plan& p, const ys_catalog& gal, const ys_catalog& ran, 
   unsigned* s_off = p.d_tile_off;
   unsigned* s_cur = p.d_tile_cur;
   float4* s_rec = p.d_rec;
-  int* s_cell = p.d_rec_cell;
   p.d_tile_count = reinterpret_cast<unsigned*>(b);
   p.d_tile_off = reinterpret_cast<unsigned*>(b + off_off);
   p.d_tile_cur = reinterpret_cast<unsigned*>(b + off_cur);
   p.d_rec = reinterpret_cast<float4*>(b + off_rec);
-  p.d_rec_cell = reinterpret_cast<int*>(b + off_cell);
   e = launch_assign(p, gal, ran);
   p.d_tile_count = s_count;
   p.d_tile_off = s_off;
   p.d_tile_cur = s_cur;
   p.d_rec = s_rec;
-  p.d_rec_cell = s_cell;
   if (e != cudaSuccess) {
     why = cudaGetErrorString(e);
     return YS_ERR_CUDA;

@@ -77,8 +77,7 @@ struct Plan {
   unsigned* d_tile_count = nullptr;  // [ntiles]
   unsigned* d_tile_off = nullptr;    // [ntiles + 1]
   unsigned* d_tile_cur = nullptr;    // [ntiles]
-  float4* d_rec = nullptr;       // [rec_cap] (dx, dy, dz, signed weight)
-  int* d_rec_cell = nullptr;     // [rec_cap] packed cell index
+  float4* d_rec = nullptr;       // [rec_cap] (x, y, z, signed weight) per (particle, tile)
   int64_t rec_cap = 0;
   int64_t part_cap = 0;
   // host staging for ys_estimate_host
