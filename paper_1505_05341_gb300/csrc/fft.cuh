@@ -237,6 +237,69 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
   }
 }
 
+// Out-of-place stage: reads the lines from src and writes them to dst (no barrier
+// inside; the caller synchronises before dst is read).  With two buffers a stage
+// needs one barrier instead of the two an in-place stage needs.
+template <int N, int S, bool LF>
+__device__ __forceinline__ void fft_stage_oop(const float2* src, float2* dst, int es, int ls, int nl,
+                                              const float2* tw) {
+  constexpr int R = fft_radix(N, S);
+  constexpr int E = LF ? fft_elems_lf(N) : fft_elems(N);
+  constexpr int TPL = N / E;
+  constexpr int NB = E / R;
+  constexpr int NS = fft_ns_before(N, S);
+  constexpr int STRIDE = N / R;
+  const float2* tws = tw + fft_tw_offset(N, S);
+  const int tid = threadIdx.x;
+  const int lpp = blockDim.x / TPL;
+  const bool in_pass = tid < lpp * TPL;
+  const int lane_line = LF ? tid % lpp : tid / TPL;
+  const int tl = LF ? tid / lpp : tid % TPL;
+#pragma unroll 1
+  for (int base_line = 0; base_line < nl; base_line += lpp) {
+    const int line = base_line + lane_line;
+    if (!in_pass || line >= nl) continue;
+    const float2* lp = src + line * ls;
+    float2* lq = dst + line * ls;
+    float2 v[E];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = tl + q * TPL;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = lp[(j + r * STRIDE) * es];
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int j = tl + q * TPL;
+      const int k = j % NS;
+      if (NS > 1) {
+        const float2* tk = tws + k * (R - 1);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], tk[r - 1]);
+      }
+      Dft<R>::run(&v[q * R]);
+      const int outb = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) lq[(outb + r * NS) * es] = v[q * R + r];
+    }
+  }
+}
+
+// Stages [S, END) alternating between buffers a and b (CTA-wide barrier after each);
+// the result sits in a when END - S is even, else in b.
+template <int N, int S, int END, bool Done = (S >= END)>
+struct FftPingPong {
+  __device__ static __forceinline__ void run(float2* a, float2* b, int es, int ls, int nl, const float2* tw) {
+    fft_stage_oop<N, S, true>(a, b, es, ls, nl, tw);
+    __syncthreads();
+    FftPingPong<N, S + 1, END>::run(b, a, es, ls, nl, tw);
+  }
+};
+template <int N, int S, int END>
+struct FftPingPong<N, S, END, true> {
+  __device__ static __forceinline__ void run(float2*, float2*, int, int, int, const float2*) {}
+};
+
 // Terminate the recursion at S == number of stages.
 template <int N, int S, bool LF, bool PAD = false, int NL = 0, bool Done = (S >= fft_nstages(N))>
 struct FftRun {

@@ -394,7 +394,7 @@ __device__ __forceinline__ bool warp_segment_sum(float& v, int key) {
 }
 
 // Pencils per CTA of k_x_combine.
-__host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 1024 ? 4 : 8); }
+__host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 512 ? 4 : 8); }
 
 // ---------------------------------------------------------------------------
 // x stage: FFT along x of every (mesh, group) tile of P pencils, fed by TMA.
@@ -458,7 +458,7 @@ struct XCombine {
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
   static_assert(THREADS % 32 == 0, "threads");
   static size_t smem(int nbins) {
-    size_t b = 2 * (size_t)TILE_BYTES;                       // two tile buffers
+    size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
     b += sizeof(float) * NW * 3 * nbins;                     // per-warp float bins
     b = (b + 7) & ~size_t(7);
@@ -480,7 +480,8 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   __shared__ int s_fail;
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float2* T0 = reinterpret_cast<float2*>(base);
-  float2* tw = T0 + 2 * N * P;
+  float2* Wk = T0 + 2 * N * P;  // second buffer of the out-of-place stages
+  float2* tw = Wk + N * P;
   float2* phs = tw + N;
   float* invw = reinterpret_cast<float*>(phs + N);
   float* wbin = invw + N;
@@ -537,9 +538,11 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
       ph_pen = cmul(phs[iyk], phs[kzc]);
     }
     float2* Tb = T0 + (s & 1) * N * P;
-    FftRunTo<N, 0, fft_nstages(N) - 1, true, false>::run(Tb, P, 1, P, tw);
+    constexpr int SM_STAGES = fft_nstages(N) - 1;  // stages through shared memory
+    FftPingPong<N, 0, SM_STAGES>::run(Tb, Wk, P, 1, P, tw);
+    const float2* Tf = (SM_STAGES % 2 == 0) ? Tb : Wk;
     float2 v[E];
-    fft_last_stage_regs<N, true, false>(Tb + p, P, tl, tw, v);
+    fft_last_stage_regs<N, true, false>(Tf + p, P, tl, tw, v);
     const int pw = (gi == 0) ? 0 : (gi <= 3 ? gi - 1 : gi - 4);  // power of k_x
 #pragma unroll
     for (int q = 0; q < NBL; ++q)
