@@ -375,26 +375,4 @@ __device__ __forceinline__ void fft_stage0_regs(float2 (&v)[fft_elems(N)], float
   }
 }
 
-// Stages [S, END) only.
-template <int N, int S, int END, bool LF, bool PAD, bool Done = (S >= END)>
-struct FftRunTo {
-  __device__ static __forceinline__ void run(float2* buf, int es, int ls, int nl, const float2* tw) {
-    fft_stage<N, S, LF, PAD>(buf, es, ls, nl, tw);
-    FftRunTo<N, S + 1, END, LF, PAD>::run(buf, es, ls, nl, tw);
-  }
-};
-template <int N, int S, int END, bool LF, bool PAD>
-struct FftRunTo<N, S, END, LF, PAD, true> {
-  __device__ static __forceinline__ void run(float2*, int, int, int, const float2*) {}
-};
-
-// In-place forward FFT of nl lines held in shared memory.  Every thread of the block
-// must call it.  blockDim.x must be >= N / E.  Unless LF, the stages only
-// synchronise the threads of each line: callers reading other lines afterwards
-// need a __syncthreads() first.
-template <int N, bool LF, bool PAD = false>
-__device__ __forceinline__ void fft_smem(float2* buf, int es, int ls, int nl, const float2* tw) {
-  FftRun<N, 0, LF, PAD>::run(buf, es, ls, nl, tw);
-}
-
 }  // namespace ys

@@ -3,20 +3,21 @@
 // of Eqs. (6)-(8) and the |k|-shell sums.
 //
 // Data flow per mesh (x-major mesh F[ix][iy][iz]):
-//  k_yz_rows  one x-plane, R rows per CTA: builds the basis fields F, F', and
-//             F r_hat^a r_hat^b r_hat^c (c <= 1) at the nodes, two real fields per
-//             complex row FFT along z, splits the pair into the two half spectra
-//             (k_z <= k_z,max) and writes them to a scratch laid out [field][plane]
-//             [k_z][y] (y contiguous).
-//  k_yz_cols  one x-plane, KC k_z columns per CTA: FFT along y of every basis field,
-//             then folds them with k_y, k_z polynomial weights into the groups
-//             G_{n,p} (power p of k_x; GroupTable) and writes only the pencils
-//             (k_y, k_z) with k_y^2 + k_z^2 < n2_hi, layout [mesh][group][x][pencil].
-//  k_x_combine  P pencils per CTA: FFT along x of every group of every mesh,
-//             interlacing phase and window compensation per mode, A_0 and
-//             k^n A_n = sum_p k_x^p G_{n,p}, then w |A_0|^2, w Re A_0 A_2^*,
-//             w Re A_0 A_4^* summed per shell (warp segmented sums in float, FP64
-//             shared and global accumulators).
+//  k_yz (persistent, ticketed work list; see the block comment above YZParams)
+//     row item     one x-plane, R rows: F and 1/|r|^2 per node, then for each pair of
+//                  basis fields (F, F', F r_hat^a r_hat^b r_hat^c with c <= 1) the
+//                  two real fields as one complex FFT along z, split into the two
+//                  half spectra (k_z < nzc) and written to a ring slot laid out
+//                  [field][k_z][y] (y contiguous).
+//     column item  one k_z column of one plane: FFT along y of every basis field,
+//                  folded with k_y, k_z polynomial weights into the groups G_{n,p}
+//                  (power p of k_x; GroupTable); only the pencils (k_y, k_z) with
+//                  k_y^2 + k_z^2 < n2_hi are written, layout [mesh][group][x][pencil].
+//  k_x_combine  P pencils per CTA, tiles loaded by TMA: FFT along x of every group of
+//             every mesh, interlacing phase and window compensation per mode, A_0
+//             and k^n A_n = sum_p k_x^p G_{n,p}, then w |A_0|^2, w Re A_0 A_2^*,
+//             w Re A_0 A_4^* summed per shell (per-warp float bins folded into FP64
+//             per pencil block, FP64 global accumulators).
 //  k_finalize   alpha, I, S and Eqs. (6)-(8) per shell.
 #pragma once
 #include <cuda.h>
@@ -91,8 +92,6 @@ struct YZParams {
   long long spin_limit;  // ns
 };
 
-template <int N>
-__host__ __device__ constexpr int yz_rows() { return N >= 512 ? 8 : 16; }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -371,26 +370,6 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(
     }
     __syncthreads();  // s_item is rewritten at the top of the next round
   }
-}
-
-// Segmented (by key) inclusive sum within a warp; returns true on the last lane of
-// each run of equal keys, which then holds the run total in v.
-__device__ __forceinline__ bool warp_segment_sum(float& v, int key) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int kprev = __shfl_up_sync(full, key, 1);
-  const int knext = __shfl_down_sync(full, key, 1);
-  const bool head = lane == 0 || kprev != key;
-  const bool tail = lane == 31 || knext != key;
-  const unsigned heads = __ballot_sync(full, head);
-  const unsigned mask = heads & ((lane == 31) ? full : ((2u << lane) - 1u));
-  const int start = 31 - __clz(mask);
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float vo = __shfl_up_sync(full, v, o);
-    if (lane - o >= start) v += vo;
-  }
-  return tail;
 }
 
 // Pencils per CTA of k_x_combine.
