@@ -52,7 +52,10 @@ typedef enum { YS_NGP = 1, YS_CIC = 2, YS_TSC = 3 } ys_assign_kind;
  *  compensate 1: divide every A_n(k) by prod_i sinc(k_i H / 2)^p, p = 1, 2, 3.
  *  ell_max    0, 2 or 4: highest multipole; 1, 7 or 22 fields of Sec. 3.
  *  k_min, dk, n_bins   shells [k_min + b dk, k_min + (b+1) dk), b < n_bins <= 4096; only
- *             modes with 0 < |k| < k_Nyquist = pi N / box_len enter.
+ *             modes with 0 < |k| < k_Nyquist = pi N / box_len enter.  The x stage holds
+ *             every shell's sums in shared memory, which at 768^3 and 1024^3 fits
+ *             about 1900 and 3100 shells; ys_plan_create returns YS_ERR_UNSUPPORTED
+ *             (ys_last_cuda_error() says why) for more.
  *  alpha      < 0: alpha = sum_gal w / sum_ran w (Eq. 1); else this value.
  *  max_particles   capacity (galaxies + randoms) of the plan's particle buffers.
  *  stream     cudaStream_t to queue work on (NULL = legacy default stream). */

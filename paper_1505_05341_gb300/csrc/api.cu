@@ -17,6 +17,7 @@ namespace ys {
 template <int N> cudaError_t run_measure_n(Plan& p);
 template <int N> int yz_grid_n(int ell, cudaError_t* err);
 template <int N> int x_pencils_n();
+template <int N> size_t x_smem_n(int nbins, int nwb);
 
 thread_local std::string g_last_cuda_error;
 int yz_row_items(int n);
@@ -107,6 +108,22 @@ int x_pencils_for(int n) {
     case 512: return x_pencils_n<512>();
     case 768: return x_pencils_n<768>();
     default: return x_pencils_n<1024>();
+  }
+}
+
+size_t x_smem_for(int n, int nbins, int nwb) {
+  switch (n) {
+    case 16: return x_smem_n<16>(nbins, nwb);
+    case 32: return x_smem_n<32>(nbins, nwb);
+    case 64: return x_smem_n<64>(nbins, nwb);
+    case 96: return x_smem_n<96>(nbins, nwb);
+    case 128: return x_smem_n<128>(nbins, nwb);
+    case 192: return x_smem_n<192>(nbins, nwb);
+    case 256: return x_smem_n<256>(nbins, nwb);
+    case 384: return x_smem_n<384>(nbins, nwb);
+    case 512: return x_smem_n<512>(nbins, nwb);
+    case 768: return x_smem_n<768>(nbins, nwb);
+    default: return x_smem_n<1024>(nbins, nwb);
   }
 }
 
@@ -430,6 +447,18 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   if (e != cudaSuccess || ndev == 0) {
     ys::g_last_cuda_error = e != cudaSuccess ? cudaGetErrorString(e) : "no CUDA device";
     return YS_ERR_CUDA;
+  }
+  {  // the x stage keeps every shell's sums in shared memory
+    int dev = 0, smem_max = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) {
+      ys::g_last_cuda_error = cudaGetErrorString(e);
+      return YS_ERR_CUDA;
+    }
+    if (ys::x_smem_for(c.n_mesh, c.n_bins, 1) > (size_t)smem_max) {
+      ys::g_last_cuda_error = std::to_string(c.n_bins) + " shells do not fit the shared memory of the " +
+                              std::to_string(c.n_mesh) + "^3 x stage";
+      return YS_ERR_UNSUPPORTED;
+    }
   }
   ys_plan* h = new (std::nothrow) ys_plan;
   if (!h) return YS_ERR_OOM;

@@ -64,8 +64,14 @@ template <int N, int ELL, int M>
 cudaError_t run_x(Plan& p) {
   using XC = XCombine<N, ELL, M>;
   const int nbins = p.cfg.n_bins;
-  const size_t smem = XC::smem(nbins);
   cudaError_t err;
+  int dev0 = 0, smem_max = 0;
+  if ((err = cudaGetDevice(&dev0))) return err;
+  if ((err = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0))) return err;
+  // one float-bin copy per warp while it fits, else one shared copy (many shells)
+  const int nwb = XC::smem(nbins, XC::NW) <= (size_t)smem_max ? XC::NW : 1;
+  const size_t smem = XC::smem(nbins, nwb);
+  if (smem > (size_t)smem_max) return cudaErrorInvalidConfiguration;
   if ((err = cudaFuncSetAttribute(k_x_combine<N, ELL, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return err;
   int dev = 0, sms = 0, per = 0;
@@ -77,7 +83,7 @@ cudaError_t run_x(Plan& p) {
   const int grid = std::max(1, std::min(npb, std::max(1, per) * sms));
   LaunchScope ls(p, 6);
   k_x_combine<N, ELL, M><<<grid, XC::THREADS, smem, p.stream>>>(p.gmap, p.np_pad, p.d_pencil, p.d_tw, p.d_invw,
-                                                                 p.d_phase, p.d_lut, p.n2_hi, p.d_acc, nbins,
+                                                                 p.d_phase, p.d_lut, p.n2_hi, p.d_acc, nbins, nwb,
                                                                  p.d_sync + 2 * p.m * N + 1);
   return cudaGetLastError();
 }
@@ -85,6 +91,11 @@ cudaError_t run_x(Plan& p) {
 // Pencils per x-stage CTA for mesh size N (for the host-side padding).
 template <int N>
 int x_pencils_n() { return k3_pencils(N); }
+
+// Dynamic shared memory of the x stage for mesh size N (independent of l_max and of
+// interlacing), with nwb copies of the float shell bins.
+template <int N>
+size_t x_smem_n(int nbins, int nwb) { return XCombine<N, 4, 2>::smem(nbins, nwb); }
 
 template <int N, int ELL>
 cudaError_t run_ell(Plan& p) {

@@ -436,10 +436,12 @@ struct XCombine {
   static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
   static_assert(THREADS % 32 == 0, "threads");
-  static size_t smem(int nbins) {
+  // nwb copies of the float shell bins (one per warp when they fit; warp w adds into
+  // copy w mod nwb)
+  static size_t smem(int nbins, int nwb) {
     size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
-    b += sizeof(float) * NW * 3 * nbins;                     // per-warp float bins
+    b += sizeof(float) * nwb * 3 * nbins;                    // float bins
     b = (b + 7) & ~size_t(7);
     b += sizeof(double) * 3 * nbins;                         // per-CTA FP64 bins
     return b + 128;                                          // alignment slack
@@ -450,7 +452,8 @@ template <int N, int ELL, int M>
 __global__ void __launch_bounds__(XCombine<N, ELL, M>::THREADS)
 k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* __restrict__ pencil,
             const float2* __restrict__ tw_g, const float* __restrict__ invw_g, const float2* __restrict__ phase_g,
-            const short* __restrict__ lut, int n2_hi, double* __restrict__ acc, int nbins, int* __restrict__ err) {
+            const short* __restrict__ lut, int n2_hi, double* __restrict__ acc, int nbins, int nwb,
+            int* __restrict__ err) {
   using XC = XCombine<N, ELL, M>;
   constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, NW = XC::NW, TILES = XC::TILES, RL = XC::RL;
   constexpr int NBL = E / RL;
@@ -464,14 +467,14 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   float2* phs = tw + N;
   float* invw = reinterpret_cast<float*>(phs + N);
   float* wbin = invw + N;
-  double* cbin = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wbin + NW * 3 * nbins) + 7) & ~uintptr_t(7));
+  double* cbin = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wbin + nwb * 3 * nbins) + 7) & ~uintptr_t(7));
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < N; k += blockDim.x) {
     tw[k] = tw_g[k];
     phs[k] = phase_g[k];
     invw[k] = invw_g[k];
   }
-  for (int k = tid; k < NW * 3 * nbins; k += blockDim.x) wbin[k] = 0.f;
+  for (int k = tid; k < nwb * 3 * nbins; k += blockDim.x) wbin[k] = 0.f;
   for (int k = tid; k < 3 * nbins; k += blockDim.x) cbin[k] = 0.0;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -547,7 +550,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
     const bool complete = (mj == M - 1) && (gi == 0 || gi == 3 || gi == 8);
     if (complete) {
       const int slot = gi == 0 ? 0 : (gi == 3 ? 1 : 2);
-      float* wb = wbin + (warp * 3 + slot) * nbins;
+      float* wb = wbin + ((warp % nwb) * 3 + slot) * nbins;
 #pragma unroll
       for (int q = 0; q < NBL; ++q)
 #pragma unroll
@@ -574,7 +577,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
       __syncthreads();
       for (int b = tid; b < 3 * nbins; b += blockDim.x) {
         float sum = 0.f;
-        for (int w = 0; w < NW; ++w) {
+        for (int w = 0; w < nwb; ++w) {
           sum += wbin[w * 3 * nbins + b];
           wbin[w * 3 * nbins + b] = 0.f;
         }

@@ -173,3 +173,41 @@ def test_particle_on_node_from_above_is_inside():
     res = run_gpu(gal, ran, geo, n, bins, "tsc", True)
     assert res.status == 0
     compare(res, ref, 4, "near_nodes")
+
+
+@pytest.mark.parametrize("kind,interlace,compensate", [("cic", True, False), ("tsc", False, True),
+                                                       ("ngp", False, True)])
+def test_offset_shells_and_window_options(kind, interlace, compensate):
+    """Shells starting above k = 0 with a width that does not divide the fundamental
+    frequency, the last shell ending just below Nyquist, and the window compensation
+    switched on or off; 64^3 in an off-centre box (a ragged tail of pencil blocks)."""
+    gal, ran, geo = synth.poisson_cube(15_000, 60_000, side=700.0, center=(900.0, -300.0, 450.0), seed=91)
+    n = 64
+    k_nyq = np.pi * n / geo.box_len
+    k_min, dk = 0.013, 0.0123
+    nb = int(np.floor((k_nyq - k_min) / dk))
+    bins = BinSpec(k_min, dk, nb)
+    ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign=kind, interlace=interlace, compensate=compensate)
+    res = run_gpu(gal, ran, geo, n, bins, kind, interlace, compensate=compensate)
+    compare(res, ref, 4, f"offset_shells_{kind}_{interlace}_{compensate}")
+
+
+def test_many_shells_at_the_limit():
+    """4096 shells (the ABI's limit), most of them empty at this mesh."""
+    gal, ran, geo = synth.poisson_cube(5_000, 25_000, seed=92)
+    n = 32
+    bins = BinSpec(0.0, np.pi * n / geo.box_len / 4096, 4096)
+    ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign="cic")
+    res = run_gpu(gal, ran, geo, n, bins, "cic")
+    assert res.k.size == 4096
+    compare(res, ref, 4, "4096_shells")
+
+
+def test_too_many_shells_for_the_mesh_rejected():
+    """At 768^3 the x stage's shared memory holds about 1900 shells: more is refused
+    at plan creation, before any allocation."""
+    with pytest.raises(ys.YstatError) as ei:
+        ys.Plan(768, (0.0, 0.0, 0.0), 1000.0, assign="cic", dk=1e-4, n_bins=4096)
+    assert ei.value.status == ys.ystat.YS_ERR_UNSUPPORTED
+    with ys.Plan(768, (0.0, 0.0, 0.0), 1000.0, assign="cic", dk=1e-3, n_bins=1900) as plan:
+        assert plan.n_bins == 1900
