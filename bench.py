@@ -372,7 +372,7 @@ def run_ours(args):
         "kernels": {k: {"launches_per_step": v[0], "avg_ms": v[1], "dram_bytes_ncu": TRAFFIC.get(k)}
                     for k, v in per_cls.items()},
         "clocks": clk.summary(),
-        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 20 * (gal.n + ran.n),
+        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * gal.n + 20 * ran.n,
                 "d2h_bytes_per_step": 8 * (5 * n_bins + 5)},
         "gpu_launches": gpu_launches,
         "p0_first_bins": [float(v) for v in res.p0[:3]],

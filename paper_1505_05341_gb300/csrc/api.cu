@@ -649,7 +649,8 @@ ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalo
     const float* in[5] = {s.x, s.y, s.z, s.w, s.nbar};
     const float** outp[5] = {&d.x, &d.y, &d.z, &d.w, &d.nbar};
     for (int q = 0; q < 5; ++q) {
-      if (!in[q] || s.n == 0) {
+      // n-bar enters only through the randoms (I = alpha sum_r w^2 n-bar)
+      if (!in[q] || s.n == 0 || (q == 4 && c == 0)) {
         *outp[q] = (q < 3) ? cursor : nullptr;
         continue;
       }
