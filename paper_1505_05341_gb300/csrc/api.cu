@@ -639,6 +639,26 @@ ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalo
     if ((e = ys::dalloc(p, p.d_stage, (size_t)need))) return ys::cuda_fail(e);
     p.stage_cap = need;
   }
+  // The copies are spread over the plan's stream and up to kCopyStreams more, so that
+  // several copy engines run at once; the plan's stream waits for all of them.
+  int nstreams = 1;
+  if (!p.copy_event[0]) {
+    bool ok = cudaEventCreateWithFlags(&p.copy_event[0], cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < Plan::kCopyStreams; ++k)
+      ok = cudaStreamCreateWithFlags(&p.copy_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&p.copy_event[k + 1], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  while (nstreams <= Plan::kCopyStreams && p.copy_stream[nstreams - 1] && p.copy_event[nstreams]) ++nstreams;
+  if (!p.copy_event[0]) nstreams = 1;
+  cudaStream_t streams[Plan::kCopyStreams + 1] = {p.stream};
+  for (int k = 1; k < nstreams; ++k) streams[k] = p.copy_stream[k - 1];
+  if (nstreams > 1) {
+    if ((e = cudaEventRecord(p.copy_event[0], p.stream))) return ys::cuda_fail(e);
+    for (int k = 1; k < nstreams; ++k)
+      if ((e = cudaStreamWaitEvent(streams[k], p.copy_event[0], 0))) return ys::cuda_fail(e);
+  }
+  int next = 0;
   ys_catalog dev[2];
   const ys_catalog* src[2] = {gal, ran};
   float* cursor = p.d_stage;
@@ -654,11 +674,16 @@ ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalo
         *outp[q] = (q < 3) ? cursor : nullptr;
         continue;
       }
-      if ((e = cudaMemcpyAsync(cursor, in[q], sizeof(float) * s.n, cudaMemcpyHostToDevice, p.stream)))
+      if ((e = cudaMemcpyAsync(cursor, in[q], sizeof(float) * s.n, cudaMemcpyHostToDevice,
+                               streams[next++ % nstreams])))
         return ys::cuda_fail(e);
       *outp[q] = cursor;
       cursor += s.n;
     }
+  }
+  for (int k = 1; k < nstreams; ++k) {
+    if ((e = cudaEventRecord(p.copy_event[k], streams[k]))) return ys::cuda_fail(e);
+    if ((e = cudaStreamWaitEvent(p.stream, p.copy_event[k], 0))) return ys::cuda_fail(e);
   }
   ys_status st = ys_assign(plan, &dev[0], &dev[1]);
   if (st != YS_OK) return st;
@@ -672,6 +697,10 @@ ys_status ys_plan_destroy(ys_plan* plan) {
   else cudaDeviceSynchronize();
   if (p.measure_exec) cudaGraphExecDestroy(p.measure_exec);
   if (p.cap_stream) cudaStreamDestroy(p.cap_stream);
+  for (cudaStream_t s : p.copy_stream)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : p.copy_event)
+    if (ev) cudaEventDestroy(ev);
   for (auto& ev : p.pending) {
     cudaEventDestroy(ev.a);
     cudaEventDestroy(ev.b);

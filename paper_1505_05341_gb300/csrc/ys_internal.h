@@ -88,6 +88,11 @@ struct Plan {
   bool assigned = false;
   // CUDA graph of the measurement sequence (all pointers are plan-owned)
   cudaStream_t cap_stream = nullptr;
+  // ys_estimate_host: extra streams that carry part of the host -> device copies in
+  // parallel with the plan's stream, and the events that fork and join them
+  static constexpr int kCopyStreams = 3;
+  cudaStream_t copy_stream[kCopyStreams] = {};
+  cudaEvent_t copy_event[kCopyStreams + 1] = {};
   cudaGraphExec_t measure_exec = nullptr;
   int64_t measure_launches[YS_NUM_KERNEL_CLASSES] = {};
   // statistics and optional event profiling
