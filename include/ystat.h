@@ -128,6 +128,17 @@ ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran)
  * (doubles) asynchronously.  d_out may be NULL (the plan keeps its own copy). */
 ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out);
 
+/* Wedges P_perp (0 <= mu <= 1/2) and P_para (1/2 < mu <= 1) from the multipoles,
+ * Sec. 5, Eqs. 16-17: P_perp = P_0 - 3/8 P_2 + 15/128 P_4 and
+ * P_para = P_0 + 3/8 P_2 - 15/128 P_4, shell by shell (NaN where the shell has no
+ * modes, and meaningful for l_max = 4 plans).
+ * d_rows: n_cat result rows (DEVICE, layout of ys_measure_multipoles_async) spaced
+ * `stride` doubles apart (>= 5 n_bins + 5).  d_out (DEVICE, caller-owned): n_cat x
+ * [P_perp(n_bins) | P_para(n_bins)] doubles.  Asynchronous on stream (cudaStream_t,
+ * NULL = legacy stream). */
+ys_status ys_wedges(const double* d_rows, int32_t n_cat, int64_t stride, int32_t n_bins, double* d_out,
+                    void* stream);
+
 /* As ys_measure_multipoles_async, then waits for the stream and copies the result
  * into the caller's host arrays.  Returns YS_ERR_TIMEOUT if a bounded device-side
  * wait ran out (results invalid), else YS_ERR_ARG if ys_assign saw particles

@@ -131,6 +131,7 @@ def _lib():
         lib.ys_mlp_features.argtypes = [P, P, ctypes.c_int32, I64, ctypes.c_int32, ctypes.c_double, P, P, P, P, P]
         lib.ys_mlp_correct.argtypes = [P, P, ctypes.c_int32, I64, ctypes.c_int32, ctypes.c_double, P, P]
         lib.ys_mlp_destroy.argtypes = [P]
+        lib.ys_wedges.argtypes = [P, ctypes.c_int32, I64, ctypes.c_int32, P, P]
         lib.ys_status_string.argtypes = [ctypes.c_int]
         lib.ys_status_string.restype = ctypes.c_char_p
         lib.ys_last_cuda_error.restype = ctypes.c_char_p
@@ -140,7 +141,7 @@ def _lib():
                      "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy",
                      "ys_mlp_create", "ys_mlp_get_state", "ys_mlp_set_state", "ys_mlp_forward",
                      "ys_mlp_gradient", "ys_mlp_train_step", "ys_mlp_features", "ys_mlp_correct",
-                     "ys_mlp_destroy"):
+                     "ys_mlp_destroy", "ys_wedges"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -445,3 +446,10 @@ class Mlp:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def wedges(d_rows, n_bins, d_out, stream=None):
+    """ys_wedges: (P_perp, P_para) of Eqs. 16-17 for the result rows d_rows (device
+    float64 (n_cat, stride)) into d_out (device float64 (n_cat, 2, n_bins))."""
+    n_cat, stride = d_rows.shape
+    _check(_lib().ys_wedges(_ptr(d_rows), n_cat, stride, n_bins, _ptr(d_out), stream), "ys_wedges")
