@@ -133,13 +133,22 @@ __device__ __forceinline__ int axis_tiles(int lo, int hi, int n, int tdim, int (
   return t[0] == t[1] ? 1 : 2;
 }
 
-template <int KIND, int M, bool BIN>
-__global__ void __launch_bounds__(THREADS)
+// HIST (counting pass only): the tile counts go to a histogram in shared memory
+// (ntiles counters), added to the global counts once per CTA at the end -- a few
+// CTAs per SM and a grid-stride loop, instead of one global atomic per (particle,
+// tile) on counters that every SM contends for.
+template <int KIND, int M, bool BIN, bool HIST = false, int NT = THREADS>
+__global__ void __launch_bounds__(NT)
 k_particles(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
             const float* __restrict__ pw, const float* __restrict__ pnbar, int64_t n, int is_ran,
             Geom g, const float2* __restrict__ nodes, unsigned* __restrict__ tile_count,
             unsigned* __restrict__ tile_cur, float4* __restrict__ rec,
-            double* __restrict__ sums, double alpha_cfg) {
+            double* __restrict__ sums, double alpha_cfg, int ntiles) {
+  extern __shared__ unsigned s_hist[];
+  if (HIST) {
+    for (int t = threadIdx.x; t < ntiles; t += NT) s_hist[t] = 0u;
+    __syncthreads();
+  }
   // Compensated float sums per thread (Kahan), FP64 across threads.
   float s_w = 0.f, c_w = 0.f, s_w2 = 0.f, c_w2 = 0.f, s_w2n = 0.f, c_w2n = 0.f;
   unsigned bad = 0;
@@ -183,15 +192,21 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
         for (int c = 0; c < nt[2]; ++c) {
           const int tile = (tt[0][a] * g.tiles[1] + tt[1][b]) * g.tiles[2] + tt[2][c];
           if (!BIN) {
-            atomicAdd(&tile_count[tile], 1u);
+            if (HIST) atomicAdd(&s_hist[tile], 1u);
+            else atomicAdd(&tile_count[tile], 1u);
           } else {
             const unsigned slot = atomicAdd(&tile_cur[tile], 1u);
             rec[slot] = make_float4(x, y, z, weff);
           }
         }
   }
+  if (HIST) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntiles; t += NT)
+      if (s_hist[t]) atomicAdd(&tile_count[t], s_hist[t]);
+  }
   if (!BIN) {
-    __shared__ double red[THREADS / 32][4];
+    __shared__ double red[NT / 32][4];
     double v0 = warp_sum((double)s_w - (double)c_w);
     double v1 = warp_sum((double)s_w2 - (double)c_w2);
     double v2 = warp_sum((double)s_w2n - (double)c_w2n);
@@ -201,7 +216,7 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
     __syncthreads();
     if (threadIdx.x == 0) {
       double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-      for (int k = 0; k < THREADS / 32; ++k) { t0 += red[k][0]; t1 += red[k][1]; t2 += red[k][2]; t3 += red[k][3]; }
+      for (int k = 0; k < NT / 32; ++k) { t0 += red[k][0]; t1 += red[k][1]; t2 += red[k][2]; t3 += red[k][3]; }
       if (is_ran) {
         atomicAdd(&sums[SUM_WR], t0);
         atomicAdd(&sums[SUM_WR2], t1);
@@ -317,13 +332,37 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
   if ((err = cudaMemsetAsync(p.d_sums, 0, sizeof(double) * SUM_COUNT, st)) != cudaSuccess) return err;
   auto blocks = [](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + THREADS - 1) / THREADS, 152 * 16)); };
   const ys_catalog* cats[2] = {&gal, &ran};
+  // counting: shared-memory histograms while the tile counters fit (a few CTAs per SM)
+  constexpr int HT = 1024;
+  const size_t hist_bytes = sizeof(unsigned) * (size_t)p.ntiles;
+  const bool hist = hist_bytes <= 160u * 1024u;
+  int hist_grid = 0;
+  if (hist) {
+    int dev = 0, sms = 0, per = 0;
+    if ((err = cudaGetDevice(&dev)) || (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+      return err;
+    if ((err = cudaFuncSetAttribute(k_particles<KIND, M, false, true, HT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes)))
+      return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_particles<KIND, M, false, true, HT>, HT,
+                                                             hist_bytes)))
+      return err;
+    hist_grid = std::max(1, per) * sms;
+  }
   for (int c = 0; c < 2; ++c) {
     const ys_catalog& k = *cats[c];
     if (k.n == 0) continue;
     LaunchScope ls(p, 0);
-    k_particles<KIND, M, false><<<blocks(k.n), THREADS, 0, st>>>(
-        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr,
-        p.d_sums, p.cfg.alpha);
+    if (hist) {
+      const int grid = (int)std::min<int64_t>(hist_grid, (k.n + HT - 1) / HT);
+      k_particles<KIND, M, false, true, HT><<<grid, HT, hist_bytes, st>>>(
+          k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr,
+          p.d_sums, p.cfg.alpha, p.ntiles);
+    } else {
+      k_particles<KIND, M, false><<<blocks(k.n), THREADS, 0, st>>>(
+          k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr,
+          p.d_sums, p.cfg.alpha, p.ntiles);
+    }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   {
@@ -337,7 +376,7 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
     LaunchScope ls(p, 2);
     k_particles<KIND, M, true><<<blocks(k.n), THREADS, 0, st>>>(
         k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, nullptr, p.d_tile_cur, p.d_rec,
-        p.d_sums, p.cfg.alpha);
+        p.d_sums, p.cfg.alpha, p.ntiles);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int tvol = p.geom.tdim[0] * p.geom.tdim[1] * p.geom.tdim[2];
