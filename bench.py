@@ -163,7 +163,7 @@ def fft_flops(cls, n, m, n_pencils, nzc, pairs=8, fields=16, groups=9):
 # capture; profiles/dram_traffic_shell512_tsc_il.md).  Remove an entry when its
 # kernel changes.
 TRAFFIC = {"yz_stage": 7.90e9, "tile_deposit": 2.50e9,
-           "particle_bin": 1.19e9, "particle_count": 0.58e9}  # particle_*: mean of the galaxy and random launches
+           "particle_bin": 1.19e9}  # particle_bin: mean of the galaxy and random launches
 
 
 def kernel_bytes(cls, n_gal, n_ran, n, m, groups, n_pencils, launches_per_step, batch_planes):
