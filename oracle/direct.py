@@ -22,7 +22,7 @@ import numpy as np
 import scipy.special
 
 from .binning import BinSpec, bin_sums, half_modes, kfund, mode_bins
-from .estimator import Multipoles, legendre_combination, node_offsets, window
+from .estimator import Multipoles, legendre_combination, node_offsets, p6_combination, window
 from .normalization import catalog_sums
 
 
@@ -36,12 +36,12 @@ def _valid_modes(n, box_len, bins):
 
 
 def _point_sums(pos, wts, rel, kvec, ell_max, legendre, chunk=512):
-    """sum_p wts_p f(k_hat.r_hat_p) e^{-i k.pos_p} for f = mu^0, mu^2, mu^4 (or the
-    Legendre polynomials), for every k in kvec (M, 3)."""
+    """sum_p wts_p f(k_hat.r_hat_p) e^{-i k.pos_p} for f = mu^0, mu^2, mu^4, mu^6 (up to
+    ell_max; or the Legendre polynomials), for every k in kvec (M, 3)."""
     M = kvec.shape[0]
     kn = np.linalg.norm(kvec, axis=1)
     khat = kvec / kn[:, None]
-    outs = {n: np.zeros(M, dtype=np.complex128) for n in (0, 2, 4) if n <= ell_max}
+    outs = {n: np.zeros(M, dtype=np.complex128) for n in (0, 2, 4, 6) if n <= ell_max}
     for s in range(0, pos.shape[0], chunk):
         p = pos[s:s + chunk]
         r = rel[s:s + chunk]
@@ -72,13 +72,19 @@ def _finish(A, bidx, w, kmag, bins, norm, legendre, ell_max):
     s4 = bin_sums((A0 * np.conj(A[4])).real, bidx, w, nb) if ell_max >= 4 else np.zeros(nb)
     with np.errstate(invalid="ignore", divide="ignore"):
         kmean = ksum / nmodes
+        s6 = bin_sums((A0 * np.conj(A[6])).real, bidx, w, nb) if ell_max >= 6 else None
+        p6 = None
         if legendre:
             p0 = (s0 / nmodes - norm.S) / norm.I
             p2 = 5.0 / norm.I * s2 / nmodes
             p4 = 9.0 / norm.I * s4 / nmodes
+            if s6 is not None:
+                p6 = 13.0 / norm.I * s6 / nmodes
         else:
             p0, p2, p4 = legendre_combination(s0, s2, s4, nmodes, norm)
-    return Multipoles(kmean, nmodes, p0, p2, p4, s0, s2, s4, norm, modes=A)
+            if s6 is not None:
+                p6 = p6_combination(s0, s2, s4, s6, nmodes, norm)
+    return Multipoles(kmean, nmodes, p0, p2, p4, s0, s2, s4, norm, modes=A, p6=p6, sum6=s6)
 
 
 def sum_gal(gal, ran, geo, n_mesh: int, bins: BinSpec, alpha=None, ell_max: int = 4,

@@ -11,7 +11,9 @@ Steps, in the paper's order:
 3. One FP64 real-to-complex FFT per field (scipy.fft.rfftn, sign e^{-ik.x}).
    A_n(k) of Eq. (5) carries e^{+ik.r}; the estimator only uses Re(A_0 A_l^*), which
    is the same at k and -k for even n, so the FFT sign does not matter.
-4. A_2 from Eq. (10) and A_4 from Eq. (12), term by term (``terms``).
+4. A_2 from Eq. (10) and A_4 from Eq. (12), term by term (``terms``).  With
+   ell_max = 6 also A_6 from the 28 fields F r_x^a r_y^b r_z^c / r^6 (the same
+   decomposition one order up, ``terms.A6_TERMS``) and P_6 (``p6_combination``).
 5. Interlacing (a reading; the paper uses one CIC mesh): the second mesh has nodes
    at +H/2, so its transform carries the phase e^{-i k.(H/2)(1,1,1)};
    A = (A^(1) + e^{-i k.(H/2)(1,1,1)} A^(2)) / 2.
@@ -42,7 +44,7 @@ import scipy.fft
 from .assignment import ORDER, assign_mesh
 from .binning import BinSpec, bin_sums, half_modes, kfund, mode_bins
 from .normalization import Norm, catalog_sums
-from .terms import A2_TERMS, A4_TERMS, field_monomial
+from .terms import A2_TERMS, A4_TERMS, A6_TERMS, field_monomial
 
 
 @dataclasses.dataclass
@@ -57,6 +59,8 @@ class Multipoles:
     sum4: np.ndarray       # sum_w Re A0 A4^*
     norm: Norm
     modes: dict | None = None
+    p6: np.ndarray | None = None     # l = 6 (ell_max = 6 only)
+    sum6: np.ndarray | None = None   # sum_w Re A0 A6^*
 
 
 def legendre_combination(sum0, sum2, sum4, nmodes, norm: Norm):
@@ -69,6 +73,14 @@ def legendre_combination(sum0, sum2, sum4, nmodes, norm: Norm):
         p2 = 2.5 / norm.I * (3.0 * m2 - m0)
         p4 = 1.125 / norm.I * (35.0 * m4 - 30.0 * m2 + 3.0 * m0)
     return p0, p2, p4
+
+
+def p6_combination(sum0, sum2, sum4, sum6, nmodes, norm: Norm):
+    """P_6 = 13/I <Re A_0 [L_6 combination]^*> with L_6(mu) = (231 mu^6 - 315 mu^4
+    + 105 mu^2 - 5) / 16, the l = 6 term of Eq. (4) written with the mu-power sums."""
+    with np.errstate(invalid="ignore", divide="ignore"):
+        m0, m2, m4, m6 = (v / nmodes for v in (sum0, sum2, sum4, sum6))
+        return 13.0 / 16.0 / norm.I * (231.0 * m6 - 315.0 * m4 + 105.0 * m2 - 5.0 * m0)
 
 
 def node_offsets(box_min, box_len, n, observer, interlaced):
@@ -132,6 +144,8 @@ def mesh_transforms(F, rx, ry, rz, ell_max, workers):
     out["A2"] = assemble(A2_TERMS, inv_r2, inv_k2)
     if ell_max >= 4:
         out["A4"] = assemble(A4_TERMS, inv_r2 * inv_r2, inv_k2 * inv_k2)
+    if ell_max >= 6:
+        out["A6"] = assemble(A6_TERMS, inv_r2 ** 3, inv_k2 ** 3)
     return out
 
 
@@ -168,7 +182,11 @@ def fft_multipoles(gal, ran, geo, n_mesh: int, bins: BinSpec, assign: str = "cic
     s2 = bin_sums((A0 * np.conj(A["A2"])).real, bidx, w, nb) if ell_max >= 2 else np.zeros(nb)
     s4 = bin_sums((A0 * np.conj(A["A4"])).real, bidx, w, nb) if ell_max >= 4 else np.zeros(nb)
     p0, p2, p4 = legendre_combination(s0, s2, s4, nmodes, norm)
+    s6 = p6 = None
+    if ell_max >= 6:
+        s6 = bin_sums((A0 * np.conj(A["A6"])).real, bidx, w, nb)
+        p6 = p6_combination(s0, s2, s4, s6, nmodes, norm)
     with np.errstate(invalid="ignore", divide="ignore"):
         kmean = ksum / nmodes
     return Multipoles(kmean, nmodes, p0, p2, p4, s0, s2, s4, norm,
-                      modes=A if return_modes else None)
+                      modes=A if return_modes else None, p6=p6, sum6=s6)

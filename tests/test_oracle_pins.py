@@ -17,7 +17,7 @@ import synth
 from oracle.assignment import _stencil
 from oracle.binning import BinSpec, half_modes, mode_bins
 from oracle.estimator import node_offsets, window
-from oracle.terms import A2_TERMS, A4_TERMS, field_monomial
+from oracle.terms import A2_TERMS, A4_TERMS, A6_TERMS, field_monomial
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -45,7 +45,7 @@ def test_terms_match_printed_equations():
     assert [(c, p, n) for e, c, p, n in rows if e == "A4"] == A4_TERMS
 
 
-@pytest.mark.parametrize("terms,deg", [(A2_TERMS, 2), (A4_TERMS, 4)])
+@pytest.mark.parametrize("terms,deg", [(A2_TERMS, 2), (A4_TERMS, 4), (A6_TERMS, 6)])
 def test_terms_expand_mu_power(terms, deg):
     """sum_terms coef k^p r^m / (k^n r^n) == (k_hat . r_hat)^n on random vectors
     (the decomposition is exact, Sec. 3)."""
@@ -336,3 +336,44 @@ def test_field_identities():
     for m in range(1, n // 2):
         assert T["A2"][m, 0, 0] == pytest.approx(bxx[m, 0, 0], rel=1e-10, abs=1e-12)
         assert T["A4"][m, 0, 0] == pytest.approx(ft("Cxxx")[m, 0, 0], rel=1e-10, abs=1e-12)
+
+
+# --------------------------------------------------------------------------
+# l = 6 (the same decomposition one order up; Sec. 3)
+# --------------------------------------------------------------------------
+
+def test_l6_terms_cover_every_monomial_once():
+    assert len(A6_TERMS) == 28
+    assert len({kp for _, kp, _ in A6_TERMS}) == 28
+    assert sum(c for c, _, _ in A6_TERMS) == 3 ** 6   # (1 + 1 + 1)^6
+
+
+def test_l6_routes_agree_ngp_on_nodes():
+    """Particles on nodes + NGP + no window: the 28-field FFT route, sum-gal with
+    mu-powers and sum-gal with L_6 evaluated directly give the same P_6."""
+    n = 16
+    gal, ran, geo = synth.on_node_catalog(n, (64.0, 32.0, 96.0), 128.0, 300, 1500, seed=3)
+    bins = BinSpec(0.0, 0.02, 20)
+    f = oracle.fft_multipoles(gal, ran, geo, n, bins, assign="ngp", compensate=False, ell_max=6)
+    g = oracle.sum_gal(gal, ran, geo, n, bins, ell_max=6)
+    gl = oracle.sum_gal(gal, ran, geo, n, bins, ell_max=6, legendre=True)
+    assert _rel(f.p6, g.p6) < 1e-12
+    assert _rel(g.p6, gl.p6) < 1e-12
+    for name in ("p0", "p2", "p4"):   # adding l = 6 leaves the lower multipoles alone
+        assert _rel(getattr(f, name), getattr(g, name)) < 1e-12
+
+
+def test_l6_distant_observer_limit():
+    """Observer far along -z: A_6 -> mu^6 A_0 with mu = k_z/k at every mode."""
+    gal, ran, geo = synth.poisson_cube(1500, 7500, side=400.0, center=(0.0, 0.0, 0.0), seed=32)
+    geo = synth.Geometry(geo.box_min, geo.box_len, (0.0, 0.0, -1.0e9))
+    n = 16
+    bins = BinSpec(0.0, 0.01, 30)
+    f = oracle.fft_multipoles(gal, ran, geo, n, bins, assign="cic", ell_max=6, return_modes=True)
+    mx, my, mz, _ = half_modes(n)
+    k2 = (mx * mx + my * my + mz * mz).astype(float)
+    mu2 = np.where(k2 > 0, mz * mz / np.where(k2 > 0, k2, 1), 0)
+    A0 = f.modes["A0"]
+    bidx, _, _ = mode_bins(n, geo.box_len, bins)
+    sel = bidx >= 0
+    assert np.max(np.abs(f.modes["A6"] - mu2 ** 3 * A0)[sel]) < 1e-5 * np.max(np.abs(A0[sel]))
