@@ -14,7 +14,9 @@ fields actually transformed (the "basis") are
   in every LOS field, so the identity above only holds for F'),
   degree 2, c <= 1 : (2,0,0) (1,1,0) (0,2,0) (1,0,1) (0,1,1),
   degree 4, c <= 1 : (4,0,0) (3,1,0) (2,2,0) (1,3,0) (0,4,0) (3,0,1) (2,1,1) (1,2,1) (0,3,1).
-16 real fields = 8 complex transforms for l <= 4 (7 fields for l <= 2).
+16 real fields = 8 complex transforms for l <= 4 (7 fields for l <= 2).  For l <= 6
+the degree-6 monomials with c <= 1 add 13 fields (29 in all) and the groups
+(6, 0..6) add 7 (16 in all).
 
 Run:  python gen_group_table.py > group_table.inc
 """
@@ -27,6 +29,7 @@ from fractions import Fraction
 DEG2 = [(2, 0, 0), (1, 1, 0), (0, 2, 0), (1, 0, 1), (0, 1, 1)]
 DEG4 = [(4, 0, 0), (3, 1, 0), (2, 2, 0), (1, 3, 0), (0, 4, 0),
         (3, 0, 1), (2, 1, 1), (1, 2, 1), (0, 3, 1)]
+DEG6 = [(6 - b, b, 0) for b in range(7)] + [(5 - b, b, 1) for b in range(6)]
 
 
 def basis(ell_max):
@@ -38,6 +41,8 @@ def basis(ell_max):
         out += [m + (2,) for m in DEG2]
     if ell_max >= 4:
         out += [m + (4,) for m in DEG4]
+    if ell_max >= 6:
+        out += [m + (6,) for m in DEG6]
     return out
 
 
@@ -64,6 +69,8 @@ def groups(ell_max):
         g += [(2, p) for p in range(3)]
     if ell_max >= 4:
         g += [(4, p) for p in range(5)]
+    if ell_max >= 6:
+        g += [(6, p) for p in range(7)]
     return g
 
 
@@ -96,10 +103,11 @@ def emit(ell_max):
     lines.append("  // returns Psi_beta; combine() zeroes G and adds every basis field.")
     lines.append("  template <int LO, int HI, class PsiAt>")
     lines.append("  __device__ static __forceinline__ void accumulate(PsiAt psi, float ky, float kz, float2 (&g)[NG]) {")
-    lines.append("    float kyp[5], kzp[5];")
+    npow = max(5, ell_max + 1)
+    lines.append(f"    float kyp[{npow}], kzp[{npow}];")
     lines.append("    kyp[0] = 1.f; kzp[0] = 1.f;")
     lines.append("    #pragma unroll")
-    lines.append("    for (int i = 1; i < 5; ++i) { kyp[i] = kyp[i - 1] * ky; kzp[i] = kzp[i - 1] * kz; }")
+    lines.append(f"    for (int i = 1; i < {npow}; ++i) {{ kyp[i] = kyp[i - 1] * ky; kzp[i] = kzp[i - 1] * kz; }}")
     by_beta = {}
     for (gi, beta), poly in sorted(tab.items()):
         by_beta.setdefault(beta, []).append((gi, poly))
@@ -143,7 +151,7 @@ def main():
     print("// Generated by gen_group_table.py -- do not edit.")
     print("// Folds the y,z-transformed basis fields into powers of k_x (Eqs. 10 and 12).")
     print("template <int ELL> struct GroupTable;")
-    for ell in (0, 2, 4):
+    for ell in (0, 2, 4, 6):
         print(emit(ell))
 
 

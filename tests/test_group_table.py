@@ -1,6 +1,7 @@
-"""The library's k_x-power grouping (csrc/gen_group_table.py, 16 basis fields)
-reproduces the oracle's literal 22-field A_2 and A_4 of Eqs. (10) and (12) at every
-mode, including an observer sitting exactly on a mesh node (host-side check)."""
+"""The library's k_x-power grouping (csrc/gen_group_table.py: 16 basis fields for
+l <= 4, 29 for l <= 6) reproduces the oracle's literal 22-field A_2 and A_4 of
+Eqs. (10) and (12), and its 28-field A_6, at every mode, including an observer
+sitting exactly on a mesh node (host-side check)."""
 import importlib.util
 import os
 
@@ -32,7 +33,7 @@ def test_grouping_reproduces_eqs_10_12(center):
     rx, ry, rz = node_offsets(geo.box_min, geo.box_len, n, geo.observer, False)
     if center == (0.0, 0.0, 0.0):
         assert np.any(rx == 0) and np.any(ry == 0) and np.any(rz == 0)
-    T = mesh_transforms(F, rx, ry, rz, 4, 1)
+    T = mesh_transforms(F, rx, ry, rz, 6, 1)
     X, Y, Z = rx[:, None, None], ry[None, :, None], rz[None, None, :]
     r = np.sqrt(X * X + Y * Y + Z * Z)
     inv = np.where(r > 0, 1 / np.where(r > 0, r, 1), 0)
@@ -40,9 +41,9 @@ def test_grouping_reproduces_eqs_10_12(center):
     m = np.fft.fftfreq(n, 1 / n)
     kx, ky, kz = m[:, None, None], m[None, :, None], np.arange(n // 2 + 1)[None, None, :]
     k2 = kx ** 2 + ky ** 2 + kz ** 2
-    for ell in (2, 4):
+    for ell in (2, 4, 6):
         bs, tab, gs = G.basis(ell), G.table(ell), G.groups(ell)
-        assert len(bs) == {2: 7, 4: 16}[ell]
+        assert len(bs) == {2: 7, 4: 16, 6: 29}[ell]
         psi = []
         for (a, b, c, d) in bs:
             f = F if d == 0 else (np.where(r > 0, F, 0.0) if d == -1 else F * xh ** a * yh ** b * zh ** c)
@@ -52,7 +53,7 @@ def test_grouping_reproduces_eqs_10_12(center):
             grp[gi] = grp[gi] + sum(float(v) * ky ** b * kz ** c for (b, c), v in poly.items()) * psi[beta]
         grpx = [np.fft.fft(g_, axis=0) for g_ in grp]
         np.testing.assert_allclose(grpx[0], T["A0"], rtol=0, atol=1e-12 * np.abs(T["A0"]).max())
-        for nn, key in ((2, "A2"), (4, "A4")):
+        for nn, key in ((2, "A2"), (4, "A4"), (6, "A6")):
             if nn > ell:
                 continue
             acc = sum(kx ** p * grpx[gs.index((nn, p))] for p in range(nn + 1))
