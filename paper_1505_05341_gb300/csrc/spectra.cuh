@@ -455,7 +455,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
             const short* __restrict__ lut, int n2_hi, double* __restrict__ acc, int nbins, int nwb,
             int* __restrict__ err) {
   using XC = XCombine<N, ELL, M>;
-  constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, NW = XC::NW, TILES = XC::TILES, RL = XC::RL;
+  constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, TILES = XC::TILES, RL = XC::RL;
   constexpr int NBL = E / RL;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bar[2];
