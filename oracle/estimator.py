@@ -42,7 +42,7 @@ import numpy as np
 import scipy.fft
 
 from .assignment import ORDER, assign_mesh
-from .binning import BinSpec, bin_sums, half_modes, kfund, mode_bins
+from .binning import BinSpec, bin_sums, half_modes, mode_bins
 from .normalization import Norm, catalog_sums
 from .terms import A2_TERMS, A4_TERMS, A6_TERMS, field_monomial
 

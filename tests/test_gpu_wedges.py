@@ -8,7 +8,7 @@ import oracle
 import synth
 from oracle.binning import BinSpec
 from oracle.wedges import wedges_from_multipoles
-from test_gpu_parity import TOL, run_gpu
+from test_gpu_parity import TOL
 
 torch = pytest.importorskip("torch")
 ys = pytest.importorskip("paper_1505_05341_gb300")
