@@ -376,6 +376,14 @@ def run_ours(args):
         "gpu_launches": gpu_launches,
         "p0_first_bins": [float(v) for v in res.p0[:3]],
     }
+    if world == 1 and args.workload == WORKLOAD:
+        try:
+            cmp_ = cufft_comparison()
+            cmp_["ours_yz_plus_x_ms"] = sum(per_cls[c][0] * per_cls[c][1] for c in ("yz_stage", "x_combine")
+                                            if c in per_cls)
+            line["cufft_comparison"] = cmp_
+        except Exception as exc:  # a comparison only: never fail the benchmark for it
+            line["cufft_comparison"] = {"error": str(exc)[:200]}
     if world == 1 and not args.no_batched and args.workload == WORKLOAD:
         del dgal, dran
         plan.close()
@@ -545,6 +553,33 @@ def run_learned(steps, n_heldout=200):
             "fine": "512^3 TSC, interlaced, plain path",
             "heldout_seeds": [seeds[0], seeds[-1]],
             "trained": {k: meta[k] for k in ("train_seeds", "rows", "steps", "lr", "lr_final")}}
+
+
+def cufft_comparison(n=512, fields=16, meshes=2, reps=3):
+    """cuFFT (through torch.fft) on the same transforms, as a comparison only: one
+    full real-to-complex 3D FFT of each of the 16 basis fields of each mesh, with no
+    pruning and none of the field construction, folding, combination or shell sums
+    that the library's y,z and x stages fuse around their own transforms."""
+    import torch
+    x = torch.randn((n, n, n), device="cuda", dtype=torch.float32)
+    out = torch.empty((n, n, n // 2 + 1), device="cuda", dtype=torch.complex64)
+    for _ in range(2):
+        torch.fft.rfftn(x, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        for _ in range(fields * meshes):
+            torch.fft.rfftn(x, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del x, out
+    torch.cuda.empty_cache()
+    return {"library": "cuFFT via torch.fft.rfftn", "transforms": fields * meshes, "n": n,
+            "ms_per_catalogue": ms,
+            "what": "full 3D R2C FFTs of the 16 basis fields x 2 meshes only; no pruning, field "
+                    "construction, folding, combination or shell sums"}
 
 
 def plan_pencils(plan, with_nzc=False):
