@@ -107,3 +107,16 @@ def test_mock_sizes_are_seeded_and_in_range():
     assert a == [sg.mock_sizes(s) for s in range(10_000, 10_050)]
     assert all(200_000 <= g <= 2_000_000 and r == 5 * g for g, r in a)
     assert len({g for g, _ in a}) > 45
+
+
+@pytest.mark.parametrize("k_max,box,n", [(0.2, 500.0, 32), (0.05, 1000.0, 64), (10.0, 300.0, 16)])
+def test_half_mode_count_matches_binning(k_max, box, n):
+    """The mode count behind the galaxy-sum extrapolation equals the oracle's
+    half-grid mode weights (Hermitian weight 2 counted as two modes, halved)."""
+    from oracle.binning import BinSpec, mode_bins
+    kn = math.pi * n / box
+    top = min(k_max, kn)
+    bins = BinSpec(0.0, top / 7, 7)
+    bidx, w, _ = mode_bins(n, box, bins)
+    want = float(np.sum(w[bidx >= 0])) / 2
+    assert bench.half_modes_below(k_max, box, n) == pytest.approx(want)
