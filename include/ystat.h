@@ -124,9 +124,24 @@ ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran)
 
 /* Eqs. (4)-(13): the LOS-weighted fields, their FFTs, the k-space combination,
  * the shell sums and Eqs. (6)-(8).  Writes the device result row
- *   d_out[0 .. 5 n_bins + 3) = [k_mean | n_modes | p0 | p2 | p4 | alpha, I, S/I]
+ *   d_out[0 .. 5 n_bins + 5) = [k_mean | n_modes | p0 | p2 | p4 |
+ *                              alpha, I, S/I, particles outside the box, timeout flag]
  * (doubles) asynchronously.  d_out may be NULL (the plan keeps its own copy). */
 ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out);
+
+/* As ys_measure_multipoles_async, then waits for the stream and copies the result
+ * into the caller's host arrays.  Returns YS_ERR_TIMEOUT if a bounded device-side
+ * wait ran out (results invalid), else YS_ERR_ARG if ys_assign saw particles
+ * outside the box (results are still written). */
+ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out);
+
+/* End-to-end convenience: gal/ran hold HOST pointers (pinned or pageable); copies them
+ * to plan-owned device buffers, runs ys_assign and ys_measure_multipoles, and fills
+ * the host result.  The copies run on the plan's stream and on three internal copy
+ * streams at once (joined with events before the assignment); the galaxies' nbar is
+ * not copied (only the randoms' enters I).  Synchronous. */
+ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran,
+                           ys_result* out);
 
 /* Wedges P_perp (0 <= mu <= 1/2) and P_para (1/2 < mu <= 1) from the multipoles,
  * Sec. 5, Eqs. 16-17: P_perp = P_0 - 3/8 P_2 + 15/128 P_4 and
@@ -139,17 +154,6 @@ ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out);
 ys_status ys_wedges(const double* d_rows, int32_t n_cat, int64_t stride, int32_t n_bins, double* d_out,
                     void* stream);
 
-/* As ys_measure_multipoles_async, then waits for the stream and copies the result
- * into the caller's host arrays.  Returns YS_ERR_TIMEOUT if a bounded device-side
- * wait ran out (results invalid), else YS_ERR_ARG if ys_assign saw particles
- * outside the box (results are still written). */
-ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out);
-
-/* End-to-end convenience: gal/ran hold HOST pointers (pinned or pageable); copies them
- * to plan-owned device buffers, runs ys_assign and ys_measure_multipoles, and fills
- * the host result.  Synchronous. */
-ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran,
-                           ys_result* out);
 
 /* Per-kernel statistics (measurement support; no counterpart in the paper).
  * With profiling on, every kernel launch of the plan is bracketed by CUDA events on
