@@ -28,10 +28,11 @@ Steps, in the paper's order:
 
 Pinned by: equality with the direct sums of ``direct`` (NGP on nodes, and sum-grid
 at every mode), the distant-observer closed form, observer invariance of P_0,
-translation / axis-permutation invariance, and the Poisson shot-noise closed form
-(tests/test_oracle_pins.py).  Interlacing and compensation: parity unpinned by the
-paper (checked only against the independent sum-grid route, which builds the
-interlaced transform from the true node positions instead of a phase factor).
+translation / axis-permutation invariance, the Poisson shot-noise closed form, and,
+for interlacing and compensation, the exact alias sum of one particle (Poisson
+summation of the kernel's analytic transform: the interlaced mean keeps the aliases
+of even q_x + q_y + q_z, compensation divides by the q = 0 factor)
+(tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

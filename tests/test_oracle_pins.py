@@ -185,6 +185,86 @@ def test_poisson_shot_noise_shape(kind, closed):
     assert abs(np.mean(r) - 1.0) < 4 * err
 
 
+_ALIAS_CACHE = {}
+
+
+def _alias_sums(kind):
+    """Poisson summation of one particle's assignment along each axis, from the
+    kernel's analytic transform sinc(w/2)^p alone (none of the oracle's code):
+
+        sum_j W(u - j) e^{-i theta j} = sum_q What(theta + 2 pi q) e^{-i (theta + 2 pi q) u},
+
+    theta = 2 pi m / N over the rfftn labels.  Returns per axis (S, T) with T the
+    same sum weighted by (-1)^q, the particle's grid coordinates u and the thetas."""
+    if kind in _ALIAS_CACHE:
+        return _ALIAS_CACHE[kind]
+    n, H = 8, 1.5
+    box_min = (-3.25, 10.5, 0.75)
+    pos = np.array([[box_min[d] + H * f for d, f in enumerate((2.23, 5.71, 7.38))]], dtype=np.float32)
+    u = [(float(pos[0, d]) - box_min[d]) / H for d in range(3)]
+    p = {"ngp": 1, "cic": 2, "tsc": 3}[kind]
+    Q = 2 ** 20 if kind == "ngp" else 2 ** 16  # NGP's terms fall as 1/q, the others' as 1/q^p
+    q = np.arange(-Q, Q + 1)
+    sign = np.where(q % 2 == 0, 1.0, -1.0)
+    m_xy = np.fft.fftfreq(n, d=1.0 / n)
+    thetas = [2 * np.pi * m / n for m in (m_xy, m_xy, np.arange(n // 2 + 1))]
+    sums = []
+    for d in range(3):
+        S, T = [], []
+        frac = u[d] - math.floor(u[d])  # e^{-2 pi i q u} only needs u mod 1
+        tail = np.exp(-2j * np.pi * q * frac)
+        for th in thetas[d]:
+            om = th + 2 * np.pi * q
+            terms = np.sinc(om / (2 * np.pi)) ** p * tail * np.exp(-1j * th * u[d])
+            S.append(np.sum(terms))
+            T.append(np.sum(sign * terms))
+        sums.append((np.array(S), np.array(T)))
+    _ALIAS_CACHE[kind] = (n, H, box_min, pos, sums, thetas, p)
+    return _ALIAS_CACHE[kind]
+
+
+def _outer(a, b, c):
+    return a[:, None, None] * b[None, :, None] * c[None, None, :]
+
+
+@pytest.mark.parametrize("kind,tol", [("ngp", 3e-6), ("cic", 1e-9), ("tsc", 1e-12)])
+@pytest.mark.parametrize("interlace", [False, True])
+@pytest.mark.parametrize("compensate", [False, True])
+def test_single_particle_alias_sum(kind, tol, interlace, compensate):
+    """Interlacing and window compensation, exactly (Sec. 4's mesh step): one
+    particle of unit net weight (a galaxy of weight 7/4 and a random of weight 1 at
+    the same point, alpha = 3/4).  By Poisson summation its mesh transform is
+    prod_i S_i, S_i = sum_q What(theta_i + 2 pi q) e^{-i (theta_i + 2 pi q) u_i}.
+    The mesh at +H/2 brought back by e^{-i theta.(1,1,1)/2} carries (-1)^(q_x+q_y+q_z)
+    on each alias, so the interlaced mean keeps the aliases of even q_x + q_y + q_z:
+    (prod S + prod T) / 2.  Compensation divides by prod What(theta_i), leaving the
+    exact mode e^{-i k.(x - box_min)} plus the surviving aliases.  A flipped
+    interlacing phase or a mesh shifted the other way gives
+    (prod S + e^{+-i sum theta} prod T) / 2 instead, which is checked to be far off."""
+    n, H, box_min, pos, sums, thetas, p = _alias_sums(kind)
+    gal = synth.Catalog.from_positions(pos, 1.75, 1e-3)
+    ran = synth.Catalog.from_positions(pos, 1.0, 1e-3)
+    geo = synth.Geometry(box_min, n * H, (0.0, 0.0, 0.0))
+    res = oracle.fft_multipoles(gal, ran, geo, n, BinSpec(0.0, 0.1, 3), assign=kind, interlace=interlace,
+                                compensate=compensate, ell_max=0, alpha=0.75, return_modes=True)
+    A0 = res.modes["A0"]
+    S = _outer(*(s for s, _ in sums))
+    T = _outer(*(t for _, t in sums))
+    Wk = _outer(*(np.sinc(th / (2 * np.pi)) ** p for th in thetas)) if compensate else 1.0
+    want = (0.5 * (S + T) if interlace else S) / Wk
+    scale = np.abs(want).max()
+    assert np.abs(A0 - want).max() <= tol * scale
+    if interlace:
+        sum_th = _outer(*(np.exp(1j * th) for th in thetas))
+        for wrong in (sum_th, np.conj(sum_th)):
+            assert np.abs(A0 - 0.5 * (S + wrong * T) / Wk).max() > 0.5 * scale
+    if compensate:
+        # the unaliased mode: at low |m| the compensated value is close to e^{-i k.(x - box_min)}
+        u = [(float(pos[0, d]) - box_min[d]) / H for d in range(3)]
+        exact = _outer(*(np.exp(-1j * th * u[d]) for d, th in enumerate(thetas)))
+        assert abs(A0[1, 0, 0] - exact[1, 0, 0]) < (0.2 if kind == "ngp" else 0.06)
+
+
 # --------------------------------------------------------------------------
 # The three implementations of Sec. 4
 # --------------------------------------------------------------------------
