@@ -123,13 +123,35 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_workload(rank, name=WORKLOAD):
+def rank_seeds(rank, name=WORKLOAD):
+    """(galaxy / field seed, random seed) of a replica: every rank draws its own
+    catalogue of the same workload."""
+    base = {"shell512_tsc_il": (4, 5), "cone256_tsc_il": (2, 3)}[name]
+    return base[0] + 100 * rank, base[1] + 100 * rank
+
+
+def make_workload(rank, name=WORKLOAD, scale=1.0):
     import synth
+    sg, sr = rank_seeds(rank, name)
     if name == "shell512_tsc_il":
-        return synth.poisson_shell(10_000_000, 50_000_000, seed_gal=4 + 100 * rank, seed_ran=5 + 100 * rank)
+        return synth.poisson_shell(int(10_000_000 * scale), int(50_000_000 * scale), seed_gal=sg, seed_ran=sr)
     if name == "cone256_tsc_il":
-        return synth.zeldovich_cone(seed_field=2 + 100 * rank, seed_ran=3 + 100 * rank)
+        return synth.zeldovich_cone(int(1_000_000 * scale), int(5_000_000 * scale), seed_field=sg, seed_ran=sr)
     raise KeyError(name)
+
+
+def max_over_ranks(value, device):
+    """The slowest rank's time: the job's time for N replicas (all_reduce MAX)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, seconds):
+    """Whole-job catalogues per second: every rank processes `steps` catalogues."""
+    return world * steps / seconds
 
 
 def alg_bytes(n_gal, n_ran, n, m, groups, n_pencils):
@@ -335,11 +357,9 @@ def run_ours(args):
     st = plan.stats(reset=True)
     gpu_launches = sum(v[0] for v in st.values())
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, "cuda")
         dist.barrier()
-    value = world * args.steps / (ms / 1e3)
+    value = job_rate(world, args.steps, ms / 1e3)
 
     # Per-kernel device times: a short profiled pass (events around each launch).
     plan.set_profiling(True)
@@ -362,9 +382,7 @@ def run_ours(args):
         plan.estimate_host(hg, hr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, "cuda")
     res = plan.measure()
 
     n_pencils, nzc = plan_pencils(plan, with_nzc=True)
@@ -409,7 +427,7 @@ def run_ours(args):
                         "dram_GBps": (TRAFFIC[k] / (v[1] / 1e3) / 1e9) if k in TRAFFIC and v[1] > 0 else None}
                     for k, v in per_cls.items()},
         "clocks": clk.summary(),
-        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * gal.n + 20 * ran.n,
+        "e2e": {"value": job_rate(world, 1, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 16 * gal.n + 20 * ran.n,
                 "d2h_bytes_per_step": 8 * (5 * n_bins + 5)},
         "gpu_launches": gpu_launches,
         "p0_first_bins": [float(v) for v in res.p0[:3]],
