@@ -202,24 +202,32 @@ def kernel_bytes(cls, n_gal, n_ran, n, m, groups, n_pencils, launches_per_step, 
     return 0.0
 
 
-def cpu_sample(gal, ran, geo, frac=0.05, n_fields=7):
+def cpu_sample(gal, ran, geo, frac=0.05, n_fields=7, field_mesh=None):
     """Time the FP64 oracle on a bounded sample of the workload and extrapolate to
-    seconds per catalogue: mesh assignment of a particle subsample (scaled by
-    1/frac and by the 2 meshes), the l <= 2 field transforms of one mesh (A_0 + 6
-    B_ij; scaled to 22 fields x 2 meshes), and one pass of shell binning."""
+    seconds per catalogue: mesh assignment of a particle subsample at the workload's
+    mesh (scaled by 1/frac and by the 2 meshes), the l <= 2 field transforms of one
+    mesh (A_0 + 6 B_ij; scaled to 22 fields x 2 meshes), and one pass of shell
+    binning.  With ``field_mesh`` below the workload's mesh the field transforms and
+    the binning run on that smaller mesh and are scaled by the cell-count ratio
+    (N / n)^3: their cost is dominated by N^3 elementwise passes (measured 512^3 /
+    256^3 time ratio 8.0 for the 7 transforms)."""
     import oracle
     import synth
     from oracle.binning import BinSpec, bin_sums, mode_bins
     from oracle.estimator import mesh_transforms, node_offsets
 
     workers = _cores()
+    fm = field_mesh or N_MESH
+    vol = (N_MESH / fm) ** 3
     ng = max(1, int(gal.n * frac))
     nr = max(1, int(ran.n * frac))
     sub = lambda c, k: synth.Catalog(c.x[:k], c.y[:k], c.z[:k], c.w[:k], c.nbar[:k])
     t0 = time.perf_counter()
     F = oracle.assign_mesh(sub(gal, ng), sub(ran, nr), 0.2, geo.box_min, geo.box_len, N_MESH, "tsc", False)
     t_assign = time.perf_counter() - t0
-    rx, ry, rz = node_offsets(geo.box_min, geo.box_len, N_MESH, geo.observer, False)
+    if fm != N_MESH:
+        F = oracle.assign_mesh(sub(gal, ng), sub(ran, nr), 0.2, geo.box_min, geo.box_len, fm, "tsc", False)
+    rx, ry, rz = node_offsets(geo.box_min, geo.box_len, fm, geo.observer, False)
     ell = 2 if n_fields >= 7 else 0
     t0 = time.perf_counter()
     T = mesh_transforms(F, rx, ry, rz, ell, workers)
@@ -227,14 +235,16 @@ def cpu_sample(gal, ran, geo, frac=0.05, n_fields=7):
     nf = 7 if ell == 2 else 1
     t0 = time.perf_counter()
     bins = BinSpec.up_to(K_MAX, DK)
-    bidx, w, kmag = mode_bins(N_MESH, geo.box_len, bins)
+    bidx, w, kmag = mode_bins(fm, geo.box_len, bins)
     A0 = T["A0"]
     for key in T:
         bin_sums((A0 * np.conj(T[key])).real, bidx, w, bins.n_bins)
     t_tail = time.perf_counter() - t0
-    per_cat = t_assign / frac * 2 + t_fields / nf * 22 * 2 + t_tail * 3 / len(T)
-    sample = (f"oracle on {frac:.0%} of the particles (1 TSC mesh), {nf} of the 44 field FFTs at 512^3, "
-              f"one shell-binning pass; scaled to 2 meshes x 22 fields; {t_assign + t_fields + t_tail:.1f} s measured")
+    per_cat = t_assign / frac * 2 + (t_fields / nf * 22 * 2 + t_tail * 3 / len(T)) * vol
+    where = f"at {N_MESH}^3" if fm == N_MESH else f"at {fm}^3 scaled by (N/n)^3 = {vol:g}"
+    sample = (f"oracle on {frac:.0%} of the particles (1 TSC mesh at {N_MESH}^3), {nf} of the 44 field FFTs "
+              f"{where}, one shell-binning pass; scaled to 2 meshes x 22 fields; "
+              f"{t_assign + t_fields + t_tail:.1f} s measured")
     return per_cat, sample, workers
 
 
@@ -285,7 +295,7 @@ def run_reference(args):
     sample = ""
     cores = _cores()
     for i in range(args.warmup + args.steps):
-        per_cat, sample, cores = cpu_sample(gal, ran, geo, frac=0.02, n_fields=7)
+        per_cat, sample, cores = cpu_sample(gal, ran, geo, frac=0.01, n_fields=7, field_mesh=N_MESH // 2)
         if i >= args.warmup:
             times.append(per_cat)
     value = 1.0 / statistics.mean(times)
