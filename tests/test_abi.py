@@ -77,3 +77,47 @@ def test_no_gpu_fails_loudly():
     assert lib.ys_plan_create(ctypes.byref(_cfg()), ctypes.byref(h)) == ystat.YS_ERR_CUDA
     with pytest.raises(ys.YstatError):
         ys.Plan(32, (0.0, 0.0, 0.0), 100.0)
+
+
+# C types of the header's struct members and the ctypes types the binding must use
+_CTYPES = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+
+
+def _header_structs():
+    """{name: [(member, ctypes type)]} for every typedef struct of include/ystat.h."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(ys.__file__), "..", "include", "ystat.h")
+    text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(\w+)\s+(\d+)", text)}
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+);", text, flags=re.S):
+        members = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            m = re.fullmatch(r"(?:const\s+)?(\w+)\s*(\*?)\s*(\w+)(?:\[(\w+)\])?", decl)
+            assert m, decl
+            ctype, star, member, dim = m.groups()
+            t = ctypes.c_void_p if star else _CTYPES[ctype]
+            if dim:
+                t = t * (int(dim) if dim.isdigit() else consts[dim])
+            members.append((member, t))
+        out[name] = members
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("ys_config", "YsConfig"), ("ys_catalog", "YsCatalog"),
+                                          ("ys_result", "YsResult"), ("ys_stats", "YsStats"),
+                                          ("ys_tuning", "YsTuning")])
+def test_binding_structs_match_header(cname, pyname):
+    """Every ctypes structure of the binding has the header's members, in order, with
+    the same C types (so sizes and offsets agree)."""
+    want = _header_structs()[cname]
+    got = getattr(ystat, pyname)._fields_
+    assert [n for n, _ in got] == [n for n, _ in want]
+    for (n, t_got), (_, t_want) in zip(got, want):
+        assert ctypes.sizeof(t_got) == ctypes.sizeof(t_want), n
+        base = lambda t: getattr(t, "_type_", t)
+        assert base(t_got) == base(t_want) or (t_got is ctypes.c_void_p and t_want is ctypes.c_void_p), n
