@@ -128,7 +128,8 @@ size_t x_smem_for(int n, int nbins, int nwb) {
 }
 
 // 2D tensor map over the grouped transforms d_g: rows = (mesh, group, x), columns =
-// 2 np_pad floats (np_pad float2 pencils); box = (2 P floats, min(N, 256) rows).
+// 2 np_pad floats (np_pad float2 pencils); box = (2 P floats, x_box_rows(N) rows, a
+// divisor of N of at most 256).
 ys_status make_gmap(Plan& p) {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
