@@ -6,8 +6,8 @@ of the estimator's arithmetic: no mesh assignment, no Fourier transform of the
 density field, no binning.
 """
 from .catalogs import (Catalog, Geometry, poisson_cube, poisson_shell, zeldovich_cone,
-                       zeldovich_cube, batched_cube_specs, on_node_catalog,
+                       zeldovich_cube, batched_cube_specs, on_node_catalog, paper_cap,
                        workload)
 
 __all__ = ["Catalog", "Geometry", "poisson_cube", "poisson_shell", "zeldovich_cone",
-           "zeldovich_cube", "batched_cube_specs", "on_node_catalog", "workload"]
+           "zeldovich_cube", "batched_cube_specs", "on_node_catalog", "paper_cap", "workload"]

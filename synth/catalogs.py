@@ -218,22 +218,22 @@ def zeldovich_cone(n_gal: int = 1_000_000, n_ran: int = 5_000_000, n_mesh: int =
                    r_mean: float = 1200.0, r_sigma: float = 300.0, r_lo: float = 300.0,
                    r_hi: float = 2100.0, f_growth: float = 0.7, p_fkp: float = 1.0e4,
                    n_lattice: int = 320, field_len: float = 2048.0, seed_field: int = 2,
-                   seed_ran: int = 3, margin_cells: int = 3):
+                   seed_ran: int = 3, margin_cells: int = 3, origin: float = -64.0, box_len=None):
     """Clustered redshift-space mock in a cone (full opening 2*half_angle_deg).
 
-    Galaxies: a cubic lattice of n_lattice^3 sites over [-64, field_len-64)^3 is
+    Galaxies: a cubic lattice of n_lattice^3 sites over [origin, origin + field_len)^3 is
     displaced by Zel'dovich moves psi, then shifted along the line of sight by
     f (psi . r_hat) r_hat; sites in the cone are kept with probability proportional
     to G(r)/r^2 (G a Gaussian of mean r_mean, width r_sigma truncated to
     [r_lo, r_hi)), then exactly n_gal are drawn without replacement.
     Randoms: radii from G, directions uniform in the cone.
     nbar(r) = n_gal G(r) / (Omega r^2 int G); FKP weights w = 1/(1 + nbar p_fkp).
-    The analysis box is the bounding cube of all points plus margin_cells cells.
+    The analysis box is the bounding cube of all points plus margin_cells cells, or,
+    with box_len given, the cube of that side centred on the points' bounding box.
     """
     rng = _rng(seed_field)
     cell = field_len / n_lattice
     psi = _displacement(n_lattice, cell, rng).astype(np.float32)
-    origin = -64.0
     g1 = origin + cell * np.arange(n_lattice, dtype=np.float64)
     ax = _unit(axis)
     cos_t = math.cos(math.radians(half_angle_deg))
@@ -292,11 +292,29 @@ def zeldovich_cone(n_gal: int = 1_000_000, n_ran: int = 5_000_000, n_mesh: int =
     allpos = np.concatenate([gal.positions(), ran.positions()]).astype(np.float64)
     lo = allpos.min(axis=0)
     hi = allpos.max(axis=0)
-    ext = float(np.max(hi - lo))
-    box_len = ext * n_mesh / (n_mesh - 2 * margin_cells)
-    H = box_len / n_mesh
-    box_min = tuple(float(v) for v in (lo - margin_cells * H))
+    if box_len is None:
+        ext = float(np.max(hi - lo))
+        box_len = ext * n_mesh / (n_mesh - 2 * margin_cells)
+        H = box_len / n_mesh
+        box_min = tuple(float(v) for v in (lo - margin_cells * H))
+    else:
+        if float(np.max(hi - lo)) >= box_len:
+            raise ValueError("the points do not fit a box of side box_len")
+        box_min = tuple(float(v) for v in (0.5 * (lo + hi) - 0.5 * box_len))
     return gal, ran, Geometry(box_min, float(box_len), (0.0, 0.0, 0.0))
+
+
+def paper_cap(n_gal: int = 525_000, n_ran: int = 5_250_000, seed_field: int = 6, seed_ran: int = 7):
+    """Stand-in for the paper's workload (Sec. 4: one survey-shaped mock of ~525 000
+    galaxies with ten times as many randoms in a box of side 3500 Mpc/h): clustered
+    redshift-space galaxies in a cap of 7000 deg^2 (half-angle 48.7 deg about +z)
+    between comoving 1100 and 1900 Mpc/h (n(r) Gaussian about 1500, width 200), FKP
+    weights with P_0 = 2e4, in a 3500 Mpc/h box centred on the cap's bounding box."""
+    half = math.degrees(math.acos(1.0 - 7000.0 * (math.pi / 180.0) ** 2 / (2.0 * math.pi)))
+    return zeldovich_cone(n_gal, n_ran, n_mesh=512, half_angle_deg=half, axis=(0.0, 0.0, 1.0),
+                          r_mean=1500.0, r_sigma=200.0, r_lo=1100.0, r_hi=1900.0, p_fkp=2.0e4,
+                          n_lattice=400, field_len=3500.0, origin=-1500.0, seed_field=seed_field,
+                          seed_ran=seed_ran, box_len=3500.0)
 
 
 def zeldovich_cube(n_gal: int, n_ran: int, side: float = 500.0, center=(600.0, 600.0, 600.0),
@@ -364,6 +382,10 @@ def workload(name: str, scale: float = 1.0):
     if name == "cone256_tsc_il":
         gal, ran, geo = zeldovich_cone(int(1_000_000 * scale), int(5_000_000 * scale))
         return gal, ran, geo, dict(n_mesh=256, assign="tsc", interlace=True, ell_max=4,
+                                   k_min=0.0, dk=0.01, k_max=None)
+    if name == "paper512_cic":
+        gal, ran, geo = paper_cap(int(525_000 * scale), int(5_250_000 * scale))
+        return gal, ran, geo, dict(n_mesh=512, assign="cic", interlace=False, ell_max=4,
                                    k_min=0.0, dk=0.01, k_max=None)
     if name == "shell512_tsc_il":
         gal, ran, geo = poisson_shell(int(10_000_000 * scale), int(50_000_000 * scale))
