@@ -1,8 +1,14 @@
-"""Pins of the wedge combination (Eqs. 16-17)."""
+"""Pins of the wedges: the combination of Eqs. 16-17 and the direct-sum definition of
+Eqs. 14-15."""
+import math
+
 import numpy as np
 from numpy.polynomial import legendre
 
-from oracle.wedges import wedges_from_multipoles
+import oracle
+import synth
+from oracle.binning import BinSpec
+from oracle.wedges import wedges_from_multipoles, wedges_sum_gal
 
 
 def _mean_over(f, a, b, n=200_001):
@@ -39,14 +45,6 @@ def test_exact_for_a_degree_four_spectrum():
 # Eqs. 14-15 by their definition (direct sum)
 # --------------------------------------------------------------------------
 
-import math  # noqa: E402
-
-import pytest  # noqa: E402
-
-import oracle  # noqa: E402
-import synth  # noqa: E402
-from oracle.binning import BinSpec  # noqa: E402
-from oracle.wedges import wedges_sum_gal  # noqa: E402
 
 
 def test_direct_wedges_partition_the_monopole():
