@@ -193,7 +193,7 @@ def _displacement(n_grid: int, cell: float, rng: np.random.Generator):
     k2[0, 0, 0] = 1.0
     psi = []
     for K in (KX, KY, KZ):
-        psi.append(np.fft.irfftn(1j * K * dk / k2, s=(n_grid,) * 3))
+        psi.append(np.fft.irfftn(1j * K * dk / k2, s=(n_grid,) * 3, axes=(0, 1, 2)))
     return np.stack(psi)
 
 
