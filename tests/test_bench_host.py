@@ -120,3 +120,19 @@ def test_half_mode_count_matches_binning(k_max, box, n):
     bidx, w, _ = mode_bins(n, box, bins)
     want = float(np.sum(w[bidx >= 0])) / 2
     assert bench.half_modes_below(k_max, box, n) == pytest.approx(want)
+
+
+@pytest.mark.parametrize("n,m,groups,launches", [(512, 2, 9, 1), (256, 1, 4, 2), (128, 2, 1, 3)])
+def test_kernel_bytes_add_up_to_the_step(n, m, groups, launches):
+    """The per-kernel algorithmic bytes behind the roofline add up to the step's: the
+    deposit writes each mesh, the y,z stage reads it and writes the grouped pencils
+    (split over its launches), the x stage reads them, and the particles are read once."""
+    ng, nr, npen = 1_000_000, 5_000_000, 12_345
+    per_step = (bench.kernel_bytes("tile_deposit", ng, nr, n, m, groups, npen, 1, None)
+                + launches * bench.kernel_bytes("yz_stage", ng, nr, n, m, groups, npen, launches, None)
+                + bench.kernel_bytes("x_combine", ng, nr, n, m, groups, npen, 1, None)
+                + 16 * (ng + nr))
+    assert per_step == pytest.approx(bench.alg_bytes(ng, nr, n, m, groups, npen), rel=1e-12)
+    # the counting launches (one per catalogue) read x, y, z, w and the randoms' nbar
+    assert 2 * bench.kernel_bytes("particle_count", ng, nr, n, m, groups, npen, 1, None) == 16 * (ng + nr) + 4 * nr
+    assert bench.kernel_bytes("finalize", ng, nr, n, m, groups, npen, 1, None) == 0.0
