@@ -130,6 +130,12 @@ def rank_seeds(rank, name=WORKLOAD):
     return base[0] + 100 * rank, base[1] + 100 * rank
 
 
+def seeds_record(rank, name=WORKLOAD):
+    """The seeds of this rank's catalogue, as recorded in the result line."""
+    sg, sr = rank_seeds(rank, name)
+    return {"galaxies": sg, "randoms": sr, "rank": rank, "other_ranks": "both seeds + 100 per rank"}
+
+
 def make_workload(rank, name=WORKLOAD, scale=1.0):
     import synth
     sg, sr = rank_seeds(rank, name)
@@ -304,7 +310,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_mesh": N_MESH, "assign": "tsc", "interlace": True, "ell_max": 4,
-                   "n_gal": gal.n, "n_ran": ran.n, "k_max": K_MAX, "dk": DK},
+                   "n_gal": gal.n, "n_ran": ran.n, "k_max": K_MAX, "dk": DK, "seeds": seeds_record(0)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -428,7 +434,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "n_mesh": N_MESH, "assign": "tsc", "interlace": True, "ell_max": 4,
                    "n_gal": gal.n, "n_ran": ran.n, "k_max": K_MAX, "dk": DK, "fields": "1+6+15",
                    "l2": "inputs larger than L2 (0.96 GB catalogue, 1 GB meshes, 11 GB spectra)",
-                   "parallelism": f"replicas{world}",
+                   "parallelism": f"replicas{world}", "seeds": seeds_record(rank, args.workload),
                    "tuned": {"tile": list(tuning.tile), "yz_grid": tuning.yz_grid, "ring_lead": tuning.ring_lead}},
         "roofline": roofline,
         "step_roofline": {"bound": "hbm", "alg_bytes": b_alg, "achieved_GBps": b_alg / (ms_step / 1e3) / 1e9,
@@ -545,7 +551,7 @@ def run_batched(steps, warmup):
     return {"value": len(specs) / (ms_batch / 1e3), "unit": UNIT, "n_catalogs": len(specs),
             "ms_per_batch": ms_batch, "plain_value": len(specs) / (ms_plain / 1e3),
             "speedup_vs_plain": ms_plain / ms_batch, "meshes": meshes, "assign": "cic", "branches": 4,
-            "autotune_s": tune_s, "rows_with_errors": bad,
+            "autotune_s": tune_s, "rows_with_errors": bad, "seeds": [specs[0][0], specs[-1][0]],
             "particles": int(sum(g + r for s_, g, r, m in specs))}
 
 

@@ -136,3 +136,10 @@ def test_kernel_bytes_add_up_to_the_step(n, m, groups, launches):
     # the counting launches (one per catalogue) read x, y, z, w and the randoms' nbar
     assert 2 * bench.kernel_bytes("particle_count", ng, nr, n, m, groups, npen, 1, None) == 16 * (ng + nr) + 4 * nr
     assert bench.kernel_bytes("finalize", ng, nr, n, m, groups, npen, 1, None) == 0.0
+
+
+def test_seeds_record_matches_the_workload_seeds():
+    assert bench.seeds_record(0) == {"galaxies": 4, "randoms": 5, "rank": 0,
+                                     "other_ranks": "both seeds + 100 per rank"}
+    r = bench.seeds_record(3, "cone256_tsc_il")
+    assert (r["galaxies"], r["randoms"]) == bench.rank_seeds(3, "cone256_tsc_il") == (302, 303)
