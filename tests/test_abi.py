@@ -121,3 +121,25 @@ def test_binding_structs_match_header(cname, pyname):
         assert ctypes.sizeof(t_got) == ctypes.sizeof(t_want), n
         base = lambda t: getattr(t, "_type_", t)
         assert base(t_got) == base(t_want) or (t_got is ctypes.c_void_p and t_want is ctypes.c_void_p), n
+
+
+def test_every_header_function_is_documented():
+    """Each entry point of include/ystat.h is preceded by its own comment block (only
+    #define lines may sit between them), of some substance."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(ys.__file__), "..", "include", "ystat.h")
+    text = open(path).read()
+    names = ys.header_functions()
+    assert names
+    for name in names:
+        m = re.search(r"^[\w\s\*]*?\b" + name + r"\s*\(", text, flags=re.M)
+        assert m, name
+        before = text[:m.start()].rstrip()
+        lines = before.split("\n")
+        while lines and lines[-1].lstrip().startswith("#define"):
+            lines.pop()
+        before = "\n".join(lines).rstrip()
+        assert before.endswith("*/"), name
+        comment = before[before.rfind("/*"):]
+        assert len(comment) >= 40, (name, comment)
