@@ -125,7 +125,7 @@ def test_binding_structs_match_header(cname, pyname):
 
 def test_every_header_function_is_documented():
     """Each entry point of include/ystat.h is preceded by its own comment block (only
-    #define lines may sit between them), of some substance."""
+    #define and typedef lines may sit between them), of some substance."""
     import os
     import re
     path = os.path.join(os.path.dirname(ys.__file__), "..", "include", "ystat.h")
@@ -137,7 +137,7 @@ def test_every_header_function_is_documented():
         assert m, name
         before = text[:m.start()].rstrip()
         lines = before.split("\n")
-        while lines and lines[-1].lstrip().startswith("#define"):
+        while lines and lines[-1].lstrip().startswith(("#define", "typedef")):
             lines.pop()
         before = "\n".join(lines).rstrip()
         assert before.endswith("*/"), name
