@@ -53,9 +53,10 @@ typedef enum { YS_NGP = 1, YS_CIC = 2, YS_TSC = 3 } ys_assign_kind;
  *  ell_max    0, 2 or 4: highest multipole; 1, 7 or 22 fields of Sec. 3.
  *  k_min, dk, n_bins   shells [k_min + b dk, k_min + (b+1) dk), b < n_bins <= 4096; only
  *             modes with 0 < |k| < k_Nyquist = pi N / box_len enter.  The x stage holds
- *             every shell's sums in shared memory, which at 768^3 and 1024^3 fits
- *             about 1900 and 3100 shells; ys_plan_create returns YS_ERR_UNSUPPORTED
- *             (ys_last_cuda_error() says why) for more.
+ *             every shell's sums in shared memory (24 bytes per shell at the least);
+ *             every supported mesh fits 4096 shells, and ys_plan_create returns
+ *             YS_ERR_UNSUPPORTED (ys_last_cuda_error() says why) for a device whose
+ *             shared memory per block is too small.
  *  alpha      < 0: alpha = sum_gal w / sum_ran w (Eq. 1); else this value.
  *  max_particles   capacity (galaxies + randoms) of the plan's particle buffers.
  *  stream     cudaStream_t to queue work on (NULL = legacy default stream). */
@@ -178,6 +179,20 @@ ys_status ys_plan_set_profiling(ys_plan* plan, int enable);
  * last reset; reset != 0 clears them afterwards. */
 ys_status ys_plan_get_stats(ys_plan* plan, ys_stats* out, int reset);
 
+/* Failure-path test hook (no counterpart in the paper).  Every wait of the y,z stage
+ * (the persistent kernel of ys_measure_multipoles*) is bounded; when one runs out the
+ * kernel stops, the call reports YS_ERR_TIMEOUT and the next measurement on the plan
+ * starts clean.  This call shortens that bound and can make one wait run out on
+ * purpose, so that the path can be exercised without any fault:
+ *  wait_limit_ns  bound of each wait in ns (<= 0: the default, 1 s; at most 10 s).
+ *  skip_plane     -1: normal operation.  0 <= skip_plane < m N (m = 2 when interlaced):
+ *                 the row items of that x-plane finish their work but withhold their
+ *                 completion signal, so the column items waiting for it time out.
+ * Waits for the plan's stream, and drops the plan's captured measurement graph (the
+ * next measurement captures it again with these settings).  YS_ERR_ARG for values
+ * out of range. */
+ys_status ys_plan_set_fault_injection(ys_plan* plan, int64_t wait_limit_ns, int32_t skip_plane);
+
 /* ys_assign without any device allocation.  (The paper has no counterpart; this is
  * a deployment variant of the assignment step.)
  *
@@ -196,10 +211,13 @@ ys_status ys_plan_get_stats(ys_plan* plan, ys_stats* out, int reset);
  * and catalogue sums, consumed by the next ys_measure_multipoles*.  Asynchronous on
  * the plan's stream.
  * Limits: the records need (gal->n + ran->n) * T * 16 bytes, T = 2^(axes with more
- * than one 16/16/32-node tile) <= 8, plus 12 bytes per tile; a catalogue that does
- * not fit returns YS_ERR_UNSUPPORTED before any work is queued (ys_last_cuda_error()
- * then gives the sizes).  For a 256^3 mesh (T = 8) this is about 520 000 particles.
- * Set-up: the first call on each device looks up the array's device address with
+ * than one tile in the plan's current scatter-tile shape) <= 8 -- 16 x 16 x 32 nodes
+ * unless ys_plan_autotune picked another shape -- plus 12 bytes per tile; a catalogue
+ * that does not fit returns YS_ERR_UNSUPPORTED before any work is queued
+ * (ys_last_cuda_error() then gives the sizes).  For a 256^3 mesh (T = 8) this is
+ * about 520 000 particles.
+ * Set-up: the first call on each device (and the first after that device's context
+ * changed, e.g. after cudaDeviceReset) looks up the array's device address with
  * cudaGetSymbolAddress while that device is current; make that first call before
  * any stream capture.
  * Sharing: every call, on every plan, uses the same array and leaves its contents

@@ -712,6 +712,23 @@ ys_status ys_plan_destroy(ys_plan* plan) {
   return YS_OK;
 }
 
+ys_status ys_plan_set_fault_injection(ys_plan* plan, int64_t wait_limit_ns, int32_t skip_plane) {
+  if (!plan) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  if (skip_plane < -1 || skip_plane >= p.m * p.n) return YS_ERR_ARG;
+  const long long limit = wait_limit_ns > 0 ? (long long)wait_limit_ns : 1000000000LL;
+  if (limit > 10000000000LL) return YS_ERR_ARG;
+  if (p.stream) cudaStreamSynchronize(p.stream);
+  p.yz_wait_ns = limit;
+  p.fault_skip_plane = skip_plane;
+  // the captured measurement graph holds the old kernel parameters: capture again
+  if (p.measure_exec) {
+    cudaGraphExecDestroy(p.measure_exec);
+    p.measure_exec = nullptr;
+  }
+  return YS_OK;
+}
+
 ys_status ys_plan_set_profiling(ys_plan* plan, int enable) {
   if (!plan) return YS_ERR_ARG;
   plan->p.profiling = enable != 0;

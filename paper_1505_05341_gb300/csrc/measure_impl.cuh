@@ -52,7 +52,8 @@ cudaError_t run_yz(Plan& p) {
   prm.m = p.m;
   prm.S = p.ring_slots;
   prm.D = p.ring_lead;
-  prm.spin_limit = 1000000000;  // 1 s, then the kernel reports a timeout
+  prm.spin_limit = p.yz_wait_ns;  // 1 s unless a test shortened it; then the kernel reports a timeout
+  prm.skip_plane = p.fault_skip_plane;
   if ((err = cudaFuncSetAttribute(k_yz<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem)))
     return err;
   LaunchScope ls(p, 4);

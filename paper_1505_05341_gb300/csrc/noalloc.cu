@@ -28,19 +28,41 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[MAX_DEVICES] = {};
+void* g_scratch_ctx[MAX_DEVICES] = {};  // context the address was looked up in
 
-// Device address of the scratch on the current device (looked up once per device).
+// The current CUDA context (driver handle), through the runtime's driver entry point.
+cudaError_t current_context(void** ctx) {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (!f || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    fn = reinterpret_cast<GetCurrent>(f);
+  }
+  return fn(ctx) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of the scratch on the current device, looked up once per device
+// with that device current, and again if the device's context has changed since
+// (after cudaDeviceReset the module, and the array with it, is loaded anew).
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  // (a null context here -- none made current yet -- only costs one more lookup later)
+  void* ctx = nullptr;
+  if ((e = current_context(&ctx)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = ptr;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;

@@ -16,8 +16,10 @@
 //  k_x_combine  P pencils per CTA, tiles loaded by TMA: FFT along x of every group of
 //             every mesh, interlacing phase and window compensation per mode, A_0
 //             and k^n A_n = sum_p k_x^p G_{n,p}, then w |A_0|^2, w Re A_0 A_2^*,
-//             w Re A_0 A_4^* summed per shell (per-warp float bins folded into FP64
-//             per pencil block, FP64 global accumulators).
+//             w Re A_0 A_4^* summed per shell: per-warp float bins, each with a
+//             companion bin that collects the exact rounding error of every add
+//             (so the pair carries the sum to ~2^-48), folded into the FP64 global
+//             accumulators once per CTA.
 //  k_finalize   alpha, I, S and Eqs. (6)-(8) per shell.
 #pragma once
 #include <cuda.h>
@@ -90,6 +92,7 @@ struct YZParams {
   int* err;              // [1]
   int nzc, np, m, S, D;
   long long spin_limit;  // ns
+  int skip_plane;        // >= 0: that plane's row items withhold their completion (test hook)
 };
 
 
@@ -354,7 +357,8 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(
         const float* rel = prm.rel + (size_t)j * 3 * N;
         row_item<N, ELL>(work, nodes, prm.mesh + j * n3 + (size_t)ix * N * N, rel[ix], rel + N, rel + 2 * N, sub * R,
                          tw, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc);
-        signal_release(prm.done_z + p);
+        if (p != prm.skip_plane) signal_release(prm.done_z + p);
+        else __syncthreads();  // withheld: the column items of plane p wait until their limit
       }
     } else {
       const int p = step - prm.D;  // column item of plane p
@@ -383,7 +387,8 @@ __host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >
 // tile overlaps the FFT of this one.  The last FFT stage stays in registers: each
 // thread owns E modes (one pencil, E values of k_x) for the whole pencil block and
 // accumulates A_0 and k^n A_n there; the per-mode terms of the shell sums go to
-// per-warp float bins in shared memory, folded into FP64 bins per pencil block.
+// compensated per-warp float bins in shared memory (add_compensated), folded into
+// the FP64 accumulators when the CTA ends.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -421,6 +426,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
 }
 
+// Adds v to the float bin *sum and keeps the rounding error of that add in *err.
+// The shared-memory atomic returns the value it added to, so the stored sum is
+// fl(old + v) and Knuth's TwoSum recovers the exact error (old + v) - fl(old + v)
+// from old and v alone, whatever other threads add before or after.  Summed over
+// every add, *sum + *err equals the exact sum up to the error terms' own rounding,
+// a relative ~2^-24 of the errors themselves: the pair accumulates like FP64 on the
+// FP32 pipes (FP64 arithmetic on this GPU runs at a small fraction of FP32).  The
+// atomic flushes a subnormal sum to zero; that changes the error by less than 2^-126.
+__device__ __forceinline__ void add_compensated(float* sum, float* err, float v) {
+  const float old = atomicAdd(sum, v);
+  const float s = old + v;
+  const float vb = s - old;
+  const float e = (old - (s - vb)) + (v - vb);
+  if (e != 0.f) atomicAdd(err, e);
+}
+
 template <int N, int ELL, int M>
 struct XCombine {
   static constexpr int P = k3_pencils(N);
@@ -436,14 +457,12 @@ struct XCombine {
   static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
   static_assert(THREADS % 32 == 0, "threads");
-  // nwb copies of the float shell bins (one per warp when they fit; warp w adds into
-  // copy w mod nwb)
+  // nwb copies of the compensated float shell bins (one per warp when they fit; warp
+  // w adds into copy w mod nwb): a sum and an error term per shell and slot
   static size_t smem(int nbins, int nwb) {
     size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
-    b += sizeof(float) * nwb * 3 * nbins;                    // float bins
-    b = (b + 7) & ~size_t(7);
-    b += sizeof(double) * 3 * nbins;                         // per-CTA FP64 bins
+    b += sizeof(float) * 2 * nwb * 3 * nbins;                // float bins and their error terms
     return b + 128;                                          // alignment slack
   }
 };
@@ -466,16 +485,15 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   float2* tw = Wk + N * P;
   float2* phs = tw + N;
   float* invw = reinterpret_cast<float*>(phs + N);
-  float* wbin = invw + N;
-  double* cbin = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wbin + nwb * 3 * nbins) + 7) & ~uintptr_t(7));
+  float* wbin = invw + N;            // [nwb][3][nbins] sums
+  float* wcmp = wbin + nwb * 3 * nbins;  // [nwb][3][nbins] their rounding errors
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < N; k += blockDim.x) {
     tw[k] = tw_g[k];
     phs[k] = phase_g[k];
     invw[k] = invw_g[k];
   }
-  for (int k = tid; k < nwb * 3 * nbins; k += blockDim.x) wbin[k] = 0.f;
-  for (int k = tid; k < 3 * nbins; k += blockDim.x) cbin[k] = 0.0;
+  for (int k = tid; k < 2 * nwb * 3 * nbins; k += blockDim.x) wbin[k] = 0.f;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -503,11 +521,15 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   int ky = 0, kz = -1, iyk = 0;
   float cf_pen = 0.f;
   float2 ph_pen = make_float2(1.f, 0.f);
+  int s_stop = total;  // step whose wait ran out (copies s_stop and s_stop + 1 may be in flight)
   for (int s = 0; s < total; ++s) {
     if (tid == 0 && s + 1 < total) issue(s + 1);
     if (!mbar_wait(&bar[s & 1], (s >> 1) & 1, 1000000000LL)) s_fail = 1;  // 1 s
     __syncthreads();
-    if (s_fail) break;
+    if (s_fail) {
+      s_stop = s;
+      break;
+    }
     const int k = s / TILES, t = s - k * TILES;
     const int gi = t / M, mj = t - gi * M;
     if (t == 0) {
@@ -551,6 +573,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
     if (complete) {
       const int slot = gi == 0 ? 0 : (gi == 3 ? 1 : 2);
       float* wb = wbin + ((warp % nwb) * 3 + slot) * nbins;
+      float* wc = wb + nwb * 3 * nbins;
 #pragma unroll
       for (int q = 0; q < NBL; ++q)
 #pragma unroll
@@ -569,33 +592,28 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
               const float inv = 1.f / (float)n2;
               val = wgt * (slot == 1 ? inv : inv * inv) * (a0[e].x * ga[e].x + a0[e].y * ga[e].y);
             }
-            atomicAdd(wb + bin, val);
+            add_compensated(wb + bin, wc + bin, val);
           }
         }
-    }
-    if (t == TILES - 1) {  // fold the float bins of this pencil block into FP64
-      __syncthreads();
-      for (int b = tid; b < 3 * nbins; b += blockDim.x) {
-        float sum = 0.f;
-        for (int w = 0; w < nwb; ++w) {
-          sum += wbin[w * 3 * nbins + b];
-          wbin[w * 3 * nbins + b] = 0.f;
-        }
-        cbin[b] += (double)sum;
-      }
     }
     __syncthreads();
   }
   if (s_fail) {
     if (tid == 0) {
       atomicExch(err, 2);
-      // let any copy still in flight land before the CTA exits (bounded)
-      for (int b = 0; b < 2; ++b) mbar_wait(&bar[b], 0, 100000000LL);  // 0.1 s
+      // Copies s_stop and s_stop + 1 (if issued) are the last ones issued into their
+      // buffers: wait for each by its own phase parity before the CTA's shared memory
+      // is released (bounded; every earlier copy has completed).
+      for (int s = s_stop; s < s_stop + 2 && s < total; ++s) mbar_wait(&bar[s & 1], (s >> 1) & 1, 100000000LL);
     }
     return;
   }
-  for (int b = tid; b < 3 * nbins; b += blockDim.x)
-    if (cbin[b] != 0.0) atomicAdd(&acc[b], cbin[b]);
+  // FP64 fold of every warp copy's sum and error term, once per CTA.
+  for (int b = tid; b < 3 * nbins; b += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nwb; ++w) v += (double)wbin[w * 3 * nbins + b] + (double)wcmp[w * 3 * nbins + b];
+    if (v != 0.0) atomicAdd(&acc[b], v);
+  }
 }
 
 }  // namespace ys

@@ -54,6 +54,8 @@ struct Plan {
   int ring_slots_cap = 0;        // ring slots allocated
   int yz_grid = 1;               // CTAs of the persistent y,z kernel
   int yz_grid_max = 1;           // resident CTAs of that kernel (upper bound for tuning)
+  long long yz_wait_ns = 1000000000LL;  // bound of each y,z-stage wait (ns)
+  int fault_skip_plane = -1;     // test hook: plane whose row items withhold their completion
   int ntiles_max = 0;            // tile-counter capacity over the scatter tile candidates
   // device tables
   float2* d_tw = nullptr;        // [n] exp(-2 pi i j / n)

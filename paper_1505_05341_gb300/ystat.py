@@ -111,6 +111,7 @@ def _lib():
         lib.ys_plan_destroy.argtypes = [P]
         lib.ys_assign_noalloc.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog)]
         lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
+        lib.ys_plan_set_fault_injection.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
         lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
         lib.ys_plan_autotune.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), ctypes.c_int32,
                                          ctypes.POINTER(YsTuning)]
@@ -138,6 +139,7 @@ def _lib():
         for name in ("ys_plan_create", "ys_assign", "ys_measure_multipoles_async",
                      "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
                      "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc", "ys_plan_autotune",
+                     "ys_plan_set_fault_injection",
                      "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy",
                      "ys_mlp_create", "ys_mlp_get_state", "ys_mlp_set_state", "ys_mlp_forward",
                      "ys_mlp_gradient", "ys_mlp_train_step", "ys_mlp_features", "ys_mlp_correct",
@@ -289,6 +291,12 @@ class Plan:
         _check(_lib().ys_plan_autotune(self._h, ctypes.byref(g), ctypes.byref(r), reps, ctypes.byref(t)),
                "ys_plan_autotune")
         return t
+
+    def set_fault_injection(self, wait_limit_ns=0, skip_plane=-1):
+        """ys_plan_set_fault_injection: bound of the y,z-stage waits, and the plane whose
+        completion is withheld (-1: none)."""
+        _check(_lib().ys_plan_set_fault_injection(self._h, int(wait_limit_ns), int(skip_plane)),
+               "ys_plan_set_fault_injection")
 
     def set_profiling(self, enable: bool):
         _check(_lib().ys_plan_set_profiling(self._h, int(bool(enable))), "ys_plan_set_profiling")
