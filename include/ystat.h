@@ -50,7 +50,11 @@ typedef enum { YS_NGP = 1, YS_CIC = 2, YS_TSC = 3 } ys_assign_kind;
  *  interlace  1: a second mesh shifted by H/2 on every axis; the two transforms are
  *             averaged with the phase e^{-i k.(H/2)(1,1,1)}.
  *  compensate 1: divide every A_n(k) by prod_i sinc(k_i H / 2)^p, p = 1, 2, 3.
- *  ell_max    0, 2 or 4: highest multipole; 1, 7 or 22 fields of Sec. 3.
+ *  ell_max    0, 2, 4 or 6: highest multipole; 1, 7 or 22 fields of Sec. 3 for l <= 4.
+ *             6 is the same decomposition one order up (the paper notes after Eq. 13
+ *             that higher orders follow alike): 28 more fields F r_i..r_n / r^6, and
+ *             P_6 = 13/I <Re A_0 A_6^*> - the l = 6 term of Eq. (4).  l_max = 6 is
+ *             supported for N <= 512 (YS_ERR_UNSUPPORTED above).
  *  k_min, dk, n_bins   shells [k_min + b dk, k_min + (b+1) dk), b < n_bins <= 4096; only
  *             modes with 0 < |k| < k_Nyquist = pi N / box_len enter.  The x stage holds
  *             every shell's sums in shared memory (24 bytes per shell at the least);
@@ -95,7 +99,8 @@ typedef struct {
  * k-space count); p0, p2, p4  the multipoles of Eqs. (6)-(8) in (Mpc/h)^3 with the
  * shot noise S/I subtracted from p0 only (Eq. 3).  Empty shells give NaN and
  * n_modes = 0.  Any array pointer may be NULL.  alpha, norm_I = alpha sum_ran w^2 nbar,
- * shot_noise = S / I with S = sum_gal w^2 + alpha^2 sum_ran w^2 are filled in. */
+ * shot_noise = S / I with S = sum_gal w^2 + alpha^2 sum_ran w^2 are filled in.
+ * p6 receives P_6 for l_max = 6 plans (NaN otherwise). */
 typedef struct {
   double* k_mean;
   double* n_modes;
@@ -105,6 +110,7 @@ typedef struct {
   double alpha;
   double norm_I;
   double shot_noise;
+  double* p6;
 } ys_result;
 
 typedef struct ys_plan_s ys_plan;
@@ -127,7 +133,8 @@ ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran)
  * the shell sums and Eqs. (6)-(8).  Writes the device result row
  *   d_out[0 .. 5 n_bins + 5) = [k_mean | n_modes | p0 | p2 | p4 |
  *                              alpha, I, S/I, particles outside the box, timeout flag]
- * (doubles) asynchronously.  d_out may be NULL (the plan keeps its own copy). */
+ * (doubles), followed for l_max = 6 by p6 in d_out[5 n_bins + 5 .. 6 n_bins + 5),
+ * asynchronously.  d_out may be NULL (the plan keeps its own copy). */
 ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out);
 
 /* As ys_measure_multipoles_async, then waits for the stream and copies the result
@@ -155,6 +162,36 @@ ys_status ys_estimate_host(ys_plan* plan, const ys_catalog* gal, const ys_catalo
 ys_status ys_wedges(const double* d_rows, int32_t n_cat, int64_t stride, int32_t n_bins, double* d_out,
                     void* stream);
 
+
+/* Sec. 4's "sum-gal": the estimator as a direct sum over galaxies and randoms,
+ *   A_n(k) = sum_p s_p w_p (k_hat . r_hat_p)^n e^{-i k.x_p},  s = +1 (galaxies), -alpha (randoms),
+ * r_p = x_p - observer the particle's own line of sight, at every half-grid mode
+ * k = k_F m (k_F = 2 pi / box_len; m_x, m_y in [-n_mesh/2, n_mesh/2), m_z in
+ * [0, n_mesh/2], weight 2 for 0 < m_z < n_mesh/2) with 0 < |k| < k_F n_mesh / 2 that
+ * falls in a shell, then Eqs. (6)-(8) (and P_6 for l_max = 6).  No mesh, window or
+ * aliasing: n_mesh only sets the k lattice (any even value 4..16384, not only FFT
+ * sizes), so the sum reaches beyond any mesh's Nyquist frequency.  Its cost is
+ * (galaxies + randoms) x modes, for small cases and as the reference the paper
+ * compares the FFT method with.
+ * cfg: n_mesh, box_min, box_len, observer, ell_max, k_min, dk, n_bins, alpha, stream are
+ * used (assign, interlace, compensate, max_particles are ignored).  gal, ran: DEVICE
+ * pointers, as for ys_assign.  d_out (DEVICE): one result row in the layout of
+ * ys_measure_multipoles_async (its last two scalars are 0).  d_wedges (DEVICE, may be
+ * NULL): [P_perp(n_bins) | P_para(n_bins)] by the wedges' definition, Sec. 5
+ * Eqs. 14-15 in the Yamamoto form: the top hat Theta(|k_hat . r_hat_p| <= 1/2) on
+ * one particle of each pair in place of L_l, normalised by 1 / (1/2), minus S/I.
+ * Allocates scratch (cudaMalloc) and waits for the stream: synchronous. */
+ys_status ys_sum_gal(const ys_config* cfg, const ys_catalog* gal, const ys_catalog* ran, double* d_out,
+                     double* d_wedges);
+
+/* Sec. 4's "sum-grid": the same direct sum over the nodes of the plan's assigned
+ * mesh(es) (after ys_assign), each node carrying F with r = node - observer as in the
+ * FFT path; an interlaced pair is averaged (nodes at +H/2 on the second mesh) and,
+ * if the plan compensates, the window is divided out.  It is the exact DFT of what
+ * the FFT path transforms, at the plan's modes and shells: the two agree shell by
+ * shell to float rounding.  Cost: filled nodes x modes (meshes up to ~64^3).
+ * d_out, d_wedges as for ys_sum_gal.  YS_ERR_STATE before ys_assign.  Synchronous. */
+ys_status ys_sum_grid(ys_plan* plan, double* d_out, double* d_wedges);
 
 /* Per-kernel statistics (measurement support; no counterpart in the paper).
  * With profiling on, every kernel launch of the plan is bracketed by CUDA events on
@@ -260,7 +297,8 @@ typedef struct ys_batch_s ys_batch;
  * (1..32); each (branch, configuration) pair gets its own plan.  Host-side. */
 ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys_batch** out);
 
-/* Doubles between consecutive result rows of ys_batch_run: 5 n_bins_max + 5. */
+/* Doubles between consecutive result rows of ys_batch_run: the longest row of the
+ * batch (5 n_bins + 5, plus n_bins for l_max = 6 plans). */
 int64_t ys_batch_result_stride(const ys_batch* batch);
 
 /* Autotune every plan of the batch on its largest catalogue (DEVICE pointers,

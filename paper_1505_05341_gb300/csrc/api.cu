@@ -17,7 +17,7 @@ namespace ys {
 template <int N> cudaError_t run_measure_n(Plan& p);
 template <int N> int yz_grid_n(int ell, cudaError_t* err);
 template <int N> int x_pencils_n();
-template <int N> size_t x_smem_n(int nbins, int nwb);
+template <int N> size_t x_smem_n(int nbins, int nwb, int ell);
 
 thread_local std::string g_last_cuda_error;
 int yz_row_items(int n);
@@ -62,6 +62,8 @@ void free_all(Plan& p) {
   p.device_bytes = 0;
 }
 
+// Result row: [k_mean | n_modes | p0 | p2 | p4 | alpha, I, S/I, n_out, timeout] and, for
+// l_max = 6, p6 after the five scalars (so rows of l_max <= 4 plans keep their layout).
 __global__ void k_finalize(const double* __restrict__ acc, const double* __restrict__ shell,
                            const double* __restrict__ sums, const int* __restrict__ flags, double alpha_cfg,
                            int nbins, int ell, double* __restrict__ res) {
@@ -71,7 +73,7 @@ __global__ void k_finalize(const double* __restrict__ acc, const double* __restr
   const double nan = __longlong_as_double(0x7ff8000000000000ULL);
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
     const double nm = shell[b];
-    double km = nan, p0 = nan, p2 = nan, p4 = nan;
+    double km = nan, p0 = nan, p2 = nan, p4 = nan, p6 = nan;
     if (nm > 0.0) {
       km = shell[nbins + b] / nm;
       const double m0 = acc[b] / nm, m2 = acc[nbins + b] / nm, m4 = acc[2 * nbins + b] / nm;
@@ -79,12 +81,16 @@ __global__ void k_finalize(const double* __restrict__ acc, const double* __restr
       p0 = (m0 - S) / I;
       if (ell >= 2) p2 = 2.5 / I * (3.0 * m2 - m0);
       if (ell >= 4) p4 = 1.125 / I * (35.0 * m4 - 30.0 * m2 + 3.0 * m0);
+      // l = 6, the same step one order up: 13/I <Re A_0 L_6^*>, L_6(mu) =
+      // (231 mu^6 - 315 mu^4 + 105 mu^2 - 5) / 16 written with the mu-power sums.
+      if (ell >= 6) p6 = 0.8125 / I * (231.0 * acc[3 * nbins + b] / nm - 315.0 * m4 + 105.0 * m2 - 5.0 * m0);
     }
     res[b] = km;
     res[nbins + b] = nm;
     res[2 * nbins + b] = p0;
     res[3 * nbins + b] = p2;
     res[4 * nbins + b] = p4;
+    if (ell >= 6) res[5 * nbins + 5 + b] = p6;
   }
   if (threadIdx.x == 0) {
     res[5 * nbins + 0] = alpha;
@@ -111,19 +117,19 @@ int x_pencils_for(int n) {
   }
 }
 
-size_t x_smem_for(int n, int nbins, int nwb) {
+size_t x_smem_for(int n, int nbins, int nwb, int ell) {
   switch (n) {
-    case 16: return x_smem_n<16>(nbins, nwb);
-    case 32: return x_smem_n<32>(nbins, nwb);
-    case 64: return x_smem_n<64>(nbins, nwb);
-    case 96: return x_smem_n<96>(nbins, nwb);
-    case 128: return x_smem_n<128>(nbins, nwb);
-    case 192: return x_smem_n<192>(nbins, nwb);
-    case 256: return x_smem_n<256>(nbins, nwb);
-    case 384: return x_smem_n<384>(nbins, nwb);
-    case 512: return x_smem_n<512>(nbins, nwb);
-    case 768: return x_smem_n<768>(nbins, nwb);
-    default: return x_smem_n<1024>(nbins, nwb);
+    case 16: return x_smem_n<16>(nbins, nwb, ell);
+    case 32: return x_smem_n<32>(nbins, nwb, ell);
+    case 64: return x_smem_n<64>(nbins, nwb, ell);
+    case 96: return x_smem_n<96>(nbins, nwb, ell);
+    case 128: return x_smem_n<128>(nbins, nwb, ell);
+    case 192: return x_smem_n<192>(nbins, nwb, ell);
+    case 256: return x_smem_n<256>(nbins, nwb, ell);
+    case 384: return x_smem_n<384>(nbins, nwb, ell);
+    case 512: return x_smem_n<512>(nbins, nwb, ell);
+    case 768: return x_smem_n<768>(nbins, nwb, ell);
+    default: return x_smem_n<1024>(nbins, nwb, ell);
   }
 }
 
@@ -434,13 +440,17 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   *out = nullptr;
   const ys_config& c = *cfg;
   if (!ys::supported_n(c.n_mesh)) return YS_ERR_UNSUPPORTED;
+  if (c.ell_max == 6 && c.n_mesh > 512) {  // the column item's 29 lines exceed shared memory
+    ys::g_last_cuda_error = "l_max = 6 is supported up to 512^3";
+    return YS_ERR_UNSUPPORTED;
+  }
   if (!(c.box_len > 0) || !std::isfinite(c.box_len)) return YS_ERR_ARG;
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(c.box_min[a]) || !std::isfinite(c.observer[a])) return YS_ERR_ARG;
   if (c.assign < YS_NGP || c.assign > YS_TSC) return YS_ERR_ARG;
   if (c.interlace != 0 && c.interlace != 1) return YS_ERR_ARG;
   if (c.compensate != 0 && c.compensate != 1) return YS_ERR_ARG;
-  if (c.ell_max != 0 && c.ell_max != 2 && c.ell_max != 4) return YS_ERR_ARG;
+  if (c.ell_max != 0 && c.ell_max != 2 && c.ell_max != 4 && c.ell_max != 6) return YS_ERR_ARG;
   if (c.n_bins <= 0 || c.n_bins > 4096 || !(c.dk > 0) || !(c.k_min >= 0)) return YS_ERR_ARG;
   if (c.max_particles < 0) return YS_ERR_ARG;
   int ndev = 0;
@@ -455,7 +465,7 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
       ys::g_last_cuda_error = cudaGetErrorString(e);
       return YS_ERR_CUDA;
     }
-    if (ys::x_smem_for(c.n_mesh, c.n_bins, 1) > (size_t)smem_max) {
+    if (ys::x_smem_for(c.n_mesh, c.n_bins, 1, c.ell_max) > (size_t)smem_max) {
       ys::g_last_cuda_error = std::to_string(c.n_bins) + " shells do not fit the shared memory of the " +
                               std::to_string(c.n_mesh) + "^3 x stage";
       return YS_ERR_UNSUPPORTED;
@@ -470,8 +480,9 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   p.m = c.interlace ? 2 : 1;
   p.ell = c.ell_max;
   p.kind = c.assign;
-  p.nb = p.ell == 0 ? 1 : (p.ell == 2 ? 7 : 16);
-  p.ng = p.ell == 0 ? 1 : (p.ell == 2 ? 4 : 9);
+  p.nb = p.ell == 0 ? 1 : (p.ell == 2 ? 7 : (p.ell == 4 ? 16 : 29));
+  p.ng = p.ell == 0 ? 1 : (p.ell == 2 ? 4 : (p.ell == 4 ? 9 : 16));
+  p.row_len = ys::result_row_len(c.n_bins, p.ell);
   const int n = p.n;
   ys::Geom& g = p.geom;
   g.n = n;
@@ -508,8 +519,8 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, slot * p.ring_slots_cap)) ||
       (e = ys::dalloc(p, p.d_sync, (size_t)2 * p.m * n + 2)) ||
       (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np_pad))) ||
-      (e = ys::dalloc(p, p.d_acc, (size_t)3 * c.n_bins)) || (e = ys::dalloc(p, p.d_sums, (size_t)ys::SUM_COUNT)) ||
-      (e = ys::dalloc(p, p.d_result, (size_t)5 * c.n_bins + 5)) ||
+      (e = ys::dalloc(p, p.d_acc, (size_t)4 * c.n_bins)) || (e = ys::dalloc(p, p.d_sums, (size_t)ys::SUM_COUNT)) ||
+      (e = ys::dalloc(p, p.d_result, (size_t)p.row_len)) ||
       (e = ys::dalloc(p, p.d_tile_count, (size_t)p.ntiles_max)) ||
       (e = ys::dalloc(p, p.d_tile_off, (size_t)p.ntiles_max + 1)) ||
       (e = ys::dalloc(p, p.d_tile_cur, (size_t)p.ntiles_max))) {
@@ -528,7 +539,7 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
     delete h;
     return st;
   }
-  p.h_result.assign((size_t)5 * c.n_bins + 5, 0.0);
+  p.h_result.assign((size_t)p.row_len, 0.0);
   if (cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     p.cap_stream = nullptr;
@@ -598,8 +609,7 @@ ys_status ys_measure_multipoles_async(ys_plan* plan, double* d_out) {
     if (e) return ys::cuda_fail(e);
   }
   if (d_out) {
-    e = cudaMemcpyAsync(d_out, p.d_result, sizeof(double) * (5 * p.cfg.n_bins + 5), cudaMemcpyDeviceToDevice,
-                        p.stream);
+    e = cudaMemcpyAsync(d_out, p.d_result, sizeof(double) * p.row_len, cudaMemcpyDeviceToDevice, p.stream);
     if (e) return ys::cuda_fail(e);
   }
   return YS_OK;
@@ -611,7 +621,7 @@ ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out) {
   ys_status st = ys_measure_multipoles_async(plan, nullptr);
   if (st != YS_OK) return st;
   const int nb = p.cfg.n_bins;
-  cudaError_t e = cudaMemcpyAsync(p.h_result.data(), p.d_result, sizeof(double) * (5 * nb + 5),
+  cudaError_t e = cudaMemcpyAsync(p.h_result.data(), p.d_result, sizeof(double) * p.row_len,
                                   cudaMemcpyDeviceToHost, p.stream);
   if (e) return ys::cuda_fail(e);
   if ((e = cudaStreamSynchronize(p.stream))) return ys::cuda_fail(e);
@@ -619,6 +629,10 @@ ys_status ys_measure_multipoles(ys_plan* plan, ys_result* out) {
   double* dst[5] = {out->k_mean, out->n_modes, out->p0, out->p2, out->p4};
   for (int q = 0; q < 5; ++q)
     if (dst[q]) std::memcpy(dst[q], r + (size_t)q * nb, sizeof(double) * nb);
+  if (out->p6) {
+    if (p.ell >= 6) std::memcpy(out->p6, r + (size_t)5 * nb + 5, sizeof(double) * nb);
+    else for (int b = 0; b < nb; ++b) out->p6[b] = std::nan("");
+  }
   out->alpha = r[5 * nb + 0];
   out->norm_I = r[5 * nb + 1];
   out->shot_noise = r[5 * nb + 2];

@@ -80,7 +80,7 @@ ys_status capture(ys_batch* b, const ys_catalog* gal, const ys_catalog* ran, dou
     e2 = ys::launch_assign(p, gal[i], ran[i]);
     if (!e2) e2 = ys::launch_measure(p);
     if (!e2)
-      e2 = cudaMemcpyAsync(d_out + (size_t)i * b->stride, p.d_result, sizeof(double) * (5 * p.cfg.n_bins + 5),
+      e2 = cudaMemcpyAsync(d_out + (size_t)i * b->stride, p.d_result, sizeof(double) * p.row_len,
                            cudaMemcpyDeviceToDevice, p.stream);
   }
   for (int br = 1; br < b->branches && !e2; ++br) {
@@ -156,7 +156,7 @@ ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys
   }
   // one plan per (branch, class) that has catalogues, sized for its largest one
   b->plans.assign(b->branches, std::vector<ys_plan*>(reps.size(), nullptr));
-  int nb_max = 0;
+  int row_max = 0;
   for (int br = 0; br < b->branches; ++br)
     for (size_t c = 0; c < reps.size(); ++c) {
       int64_t cap = 0;
@@ -171,9 +171,9 @@ ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys
         destroy_batch(b);
         return st;
       }
-      nb_max = std::max(nb_max, cc.n_bins);
+      row_max = std::max(row_max, b->plans[br][c]->p.row_len);
     }
-  b->stride = 5 * (int64_t)nb_max + 5;
+  b->stride = row_max;
   *out = b;
   return YS_OK;
 }

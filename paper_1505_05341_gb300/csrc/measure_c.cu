@@ -4,9 +4,9 @@ namespace ys {
 template cudaError_t run_measure_n<256>(Plan&);
 template int yz_grid_n<256>(int, cudaError_t*);
 template int x_pencils_n<256>();
-template size_t x_smem_n<256>(int, int);
+template size_t x_smem_n<256>(int, int, int);
 template cudaError_t run_measure_n<384>(Plan&);
 template int yz_grid_n<384>(int, cudaError_t*);
 template int x_pencils_n<384>();
-template size_t x_smem_n<384>(int, int);
+template size_t x_smem_n<384>(int, int, int);
 }  // namespace ys

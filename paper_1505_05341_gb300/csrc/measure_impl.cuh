@@ -22,11 +22,19 @@ int yz_grid(cudaError_t* err) {
   return e ? 0 : std::max(1, per) * sms;
 }
 
+// l_max = 6 needs the 29 basis lines of a column item in shared memory: N <= 512.
+template <int N>
+constexpr bool ell6_supported() { return N <= 512; }
+
 template <int N>
 int yz_grid_n(int ell, cudaError_t* err) {
   switch (ell) {
     case 0: return yz_grid<N, 0>(err);
     case 2: return yz_grid<N, 2>(err);
+    case 6:
+      if constexpr (ell6_supported<N>()) return yz_grid<N, 6>(err);
+      if (err) *err = cudaErrorInvalidValue;
+      return 0;
     default: return yz_grid<N, 4>(err);
   }
 }
@@ -93,10 +101,12 @@ cudaError_t run_x(Plan& p) {
 template <int N>
 int x_pencils_n() { return k3_pencils(N); }
 
-// Dynamic shared memory of the x stage for mesh size N (independent of l_max and of
-// interlacing), with nwb copies of the float shell bins.
+// Dynamic shared memory of the x stage for mesh size N (independent of interlacing),
+// with nwb copies of the float shell bins.
 template <int N>
-size_t x_smem_n(int nbins, int nwb) { return XCombine<N, 4, 2>::smem(nbins, nwb); }
+size_t x_smem_n(int nbins, int nwb, int ell) {
+  return ell == 6 ? XCombine<N, 6, 2>::smem(nbins, nwb) : XCombine<N, 4, 2>::smem(nbins, nwb);
+}
 
 template <int N, int ELL>
 cudaError_t run_ell(Plan& p) {
@@ -111,11 +121,17 @@ cudaError_t run_ell(Plan& p) {
 template <int N>
 cudaError_t run_measure_n(Plan& p) {
   cudaError_t err;
-  if ((err = cudaMemsetAsync(p.d_acc, 0, sizeof(double) * 3 * p.cfg.n_bins, p.stream))) return err;
+  if ((err = cudaMemsetAsync(p.d_acc, 0, sizeof(double) * 4 * p.cfg.n_bins, p.stream))) return err;
   switch (p.ell) {
     case 0: err = run_ell<N, 0>(p); break;
     case 2: err = run_ell<N, 2>(p); break;
     case 4: err = run_ell<N, 4>(p); break;
+    case 6:
+      if constexpr (ell6_supported<N>()) {
+        err = run_ell<N, 6>(p);
+        break;
+      }
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   if (err) return err;

@@ -16,7 +16,8 @@
 //  k_x_combine  P pencils per CTA, tiles loaded by TMA: FFT along x of every group of
 //             every mesh, interlacing phase and window compensation per mode, A_0
 //             and k^n A_n = sum_p k_x^p G_{n,p}, then w |A_0|^2, w Re A_0 A_2^*,
-//             w Re A_0 A_4^* summed per shell: per-warp float bins, each with a
+//             w Re A_0 A_4^* (and w Re A_0 A_6^* for l_max = 6, the same
+//             decomposition one order up) summed per shell: per-warp float bins, each with a
 //             companion bin that collects the exact rounding error of every add
 //             (so the pair carries the sum to ~2^-48), folded into the FP64 global
 //             accumulators once per CTA.
@@ -42,23 +43,24 @@ namespace ys {
 // costs one reciprocal of |r|^2 shared by all fields plus two or three products per
 // field.
 
-// v^e for a small run-time exponent 0 <= e <= 4 (warp-uniform).
+// v^e for a small run-time exponent 0 <= e <= 7 (warp-uniform), by the bits of e.
 __device__ __forceinline__ float ipow_rt(float v, int e) {
   const float v2 = v * v;
   float r = (e & 1) ? v : 1.f;
-  if (e >= 2) r *= v2;
-  if (e >= 4) r *= v2;
+  if (e & 2) r *= v2;
+  if (e & 4) r *= v2 * v2;
   return r;
 }
 
 // Field value at a node: f the mesh value, i2 = 1/|r|^2 (0 where r = 0), z = Z, K the
-// line constant X^a Y^b; c, d warp-uniform.
+// line constant X^a Y^b; c, d warp-uniform (d = 2, 4 or 6 divides by |r|^d).
 __device__ __forceinline__ float basis_value_rt(float f, float i2, float z, float K, int c, int d) {
   if (d == 0) return f;
   if (d == -1) return i2 > 0.f ? f : 0.f;
   if (d == -2) return 0.f;
   float v = (f * K) * i2;
-  if (d == 4) v *= i2;
+  if (d >= 4) v *= i2;
+  if (d == 6) v *= i2;
   if (c) v *= z;
   return v;
 }
@@ -379,6 +381,19 @@ __global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(
 // Pencils per CTA of k_x_combine.
 __host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 512 ? 4 : 8); }
 
+// First group of the multipole that group g belongs to (groups: A_0 | l = 2, powers
+// 0..2 of k_x | l = 4, powers 0..4 | l = 6, powers 0..6), and its last.
+__host__ __device__ constexpr int group_first(int g) { return g == 0 ? 0 : (g <= 3 ? 1 : (g <= 8 ? 4 : 9)); }
+__host__ __device__ constexpr int group_last(int g) { return g == 0 ? 0 : (g <= 3 ? 3 : (g <= 8 ? 8 : 15)); }
+
+// Group transformed at tile position q of a pencil block.  For l_max = 6 the powers of
+// k_x of each multipole come highest first, so that the x stage can sum them by
+// Horner's rule (see k_x_combine); otherwise in table order.
+template <int ELL>
+__host__ __device__ constexpr int tile_group(int q) {
+  return ELL == 6 ? group_first(q) + group_last(q) - q : q;
+}
+
 // ---------------------------------------------------------------------------
 // x stage: FFT along x of every (mesh, group) tile of P pencils, fed by TMA.
 // The grouped y,z transforms are a 2D tensor [m NG N rows][np_pad pencils] of
@@ -426,20 +441,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
 }
 
-// Adds v to the float bin *sum and keeps the rounding error of that add in *err.
-// The shared-memory atomic returns the value it added to, so the stored sum is
-// fl(old + v) and Knuth's TwoSum recovers the exact error (old + v) - fl(old + v)
-// from old and v alone, whatever other threads add before or after.  Summed over
-// every add, *sum + *err equals the exact sum up to the error terms' own rounding,
-// a relative ~2^-24 of the errors themselves: the pair accumulates like FP64 on the
-// FP32 pipes (FP64 arithmetic on this GPU runs at a small fraction of FP32).  The
-// atomic flushes a subnormal sum to zero; that changes the error by less than 2^-126.
-__device__ __forceinline__ void add_compensated(float* sum, float* err, float v) {
-  const float old = atomicAdd(sum, v);
-  const float s = old + v;
-  const float vb = s - old;
-  const float e = (old - (s - vb)) + (v - vb);
-  if (e != 0.f) atomicAdd(err, e);
+// Exact rounding error (a + b) - fl(a + b) of a float add (Knuth's TwoSum).
+// The shell bins use it with shared-memory atomics: the atomic returns the value it
+// added to, so the stored sum is fl(old + v), and two_sum_err(old, v) is the exact
+// error of that add whatever other threads add before or after; it goes into a
+// companion bin.  Summed over every add, sum + companion equals the exact sum up to
+// the companion's own rounding, a relative ~2^-24 of the errors themselves: the pair
+// accumulates like FP64 on the FP32 pipes (FP64 arithmetic on this GPU runs at a
+// small fraction of FP32).  The atomic flushes a subnormal sum to zero; that changes
+// the error by less than 2^-126.
+__device__ __forceinline__ float two_sum_err(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return (a - (s - bb)) + (b - bb);
 }
 
 template <int N, int ELL, int M>
@@ -450,25 +464,29 @@ struct XCombine {
   static constexpr int THREADS = P * TPL;
   static constexpr int NW = THREADS / 32;
   static constexpr int NG = GroupTable<ELL>::NG;
+  // shell-sum slots: |A_0|^2, Re A_0 A_2^*, Re A_0 A_4^* (and Re A_0 A_6^* for l = 6)
+  static constexpr int SLOTS = ELL == 6 ? 4 : 3;
   static constexpr int TILES = NG * M;
   static constexpr int BOX_ROWS = x_box_rows(N);
   static constexpr int BOXES = N / BOX_ROWS;
   static_assert(BOXES * BOX_ROWS == N, "boxes must tile the x axis");
   static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
+  // resident CTAs per SM the register budget is set for (3 x 256 threads from 256^3 up)
+  static constexpr int MIN_BLOCKS = ((N == 256 || N == 512) && ELL <= 4) ? 3 : 1;
   static_assert(THREADS % 32 == 0, "threads");
   // nwb copies of the compensated float shell bins (one per warp when they fit; warp
   // w adds into copy w mod nwb): a sum and an error term per shell and slot
   static size_t smem(int nbins, int nwb) {
     size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
-    b += sizeof(float) * 2 * nwb * 3 * nbins;                // float bins and their error terms
+    b += sizeof(float) * 2 * nwb * SLOTS * nbins;            // float bins and their error terms
     return b + 128;                                          // alignment slack
   }
 };
 
 template <int N, int ELL, int M>
-__global__ void __launch_bounds__(XCombine<N, ELL, M>::THREADS)
+__global__ void __launch_bounds__(XCombine<N, ELL, M>::THREADS, XCombine<N, ELL, M>::MIN_BLOCKS)
 k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* __restrict__ pencil,
             const float2* __restrict__ tw_g, const float* __restrict__ invw_g, const float2* __restrict__ phase_g,
             const short* __restrict__ lut, int n2_hi, double* __restrict__ acc, int nbins, int nwb,
@@ -485,15 +503,16 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   float2* tw = Wk + N * P;
   float2* phs = tw + N;
   float* invw = reinterpret_cast<float*>(phs + N);
-  float* wbin = invw + N;            // [nwb][3][nbins] sums
-  float* wcmp = wbin + nwb * 3 * nbins;  // [nwb][3][nbins] their rounding errors
+  constexpr int SLOTS = XC::SLOTS;
+  float* wbin = invw + N;                    // [nwb][SLOTS][nbins] sums
+  float* wcmp = wbin + nwb * SLOTS * nbins;  // [nwb][SLOTS][nbins] their rounding errors
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < N; k += blockDim.x) {
     tw[k] = tw_g[k];
     phs[k] = phase_g[k];
     invw[k] = invw_g[k];
   }
-  for (int k = tid; k < 2 * nwb * 3 * nbins; k += blockDim.x) wbin[k] = 0.f;
+  for (int k = tid; k < 2 * nwb * SLOTS * nbins; k += blockDim.x) wbin[k] = 0.f;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -506,7 +525,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   const int total = mine * TILES;
   auto issue = [&](int s) {
     const int k = s / TILES, t = s - k * TILES;
-    const int gi = t / M, mj = t - gi * M;
+    const int gi = tile_group<ELL>(t / M), mj = t - (t / M) * M;
     const int pb = blockIdx.x + k * gridDim.x;
     float2* dst = T0 + (s & 1) * N * P;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -518,6 +537,8 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   if (tid == 0 && total > 0) issue(0);
   const int p = tid % P, tl = tid / P;
   float2 a0[E], ga[E];
+  float2 gl[ELL == 6 ? E : 1];  // l = 6: rounding errors of the Horner sums in ga
+  int bins[E];  // shell of each of this thread's modes in the current pencil (-1: none)
   int ky = 0, kz = -1, iyk = 0;
   float cf_pen = 0.f;
   float2 ph_pen = make_float2(1.f, 0.f);
@@ -531,7 +552,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
       break;
     }
     const int k = s / TILES, t = s - k * TILES;
-    const int gi = t / M, mj = t - gi * M;
+    const int gi = tile_group<ELL>(t / M), mj = t - (t / M) * M;
     if (t == 0) {
       const short2 pc = pencil[(blockIdx.x + k * gridDim.x) * P + p];
       ky = pc.x;
@@ -540,6 +561,15 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
       const int kzc = kz < 0 ? 0 : kz;
       cf_pen = invw[iyk] * invw[kzc] * (M == 2 ? 0.5f : 1.f);
       ph_pen = cmul(phs[iyk], phs[kzc]);
+#pragma unroll
+      for (int q = 0; q < NBL; ++q)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int kx = tl + q * TPL + r * (N / RL);
+          const int mx = kx <= N / 2 ? kx : kx - N;
+          const int n2 = mx * mx + ky * ky + kz * kz;
+          bins[q * RL + r] = (kz >= 0 && n2 < n2_hi) ? lut[n2] : -1;
+        }
     }
     float2* Tb = T0 + (s & 1) * N * P;
     constexpr int SM_STAGES = fft_nstages(N) - 1;  // stages through shared memory
@@ -547,7 +577,8 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
     const float2* Tf = (SM_STAGES % 2 == 0) ? Tb : Wk;
     float2 v[E];
     fft_last_stage_regs<N, true, false>(Tf + p, P, tl, tw, v);
-    const int pw = (gi == 0) ? 0 : (gi <= 3 ? gi - 1 : gi - 4);  // power of k_x
+    const int first = group_first(gi);
+    const int pw = gi - first;  // power of k_x
 #pragma unroll
     for (int q = 0; q < NBL; ++q)
 #pragma unroll
@@ -557,44 +588,81 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
         const int mx = kx <= N / 2 ? kx : kx - N;
         float2 X = v[e];
         if (M == 2 && mj == 1) X = cmul(X, cmul(phs[kx], ph_pen));
+        if (ELL == 6 && gi != 0) {
+          // sum_p m_x^p X_p by Horner's rule (highest power first), every step
+          // error-free: the product by the integer m_x is split exactly with an FMA
+          // and the add with TwoSum, and both errors go to gl.  The window and the
+          // interlacing mean, common to all powers, are applied at completion.
+          if (mj == 0 && gi == group_last(gi)) {
+            ga[e] = X;
+            gl[e] = make_float2(0.f, 0.f);
+          } else {
+            const float m = mj == 0 ? (float)mx : 1.f;
+            const float pr = ga[e].x * m, pi = ga[e].y * m;
+            const float er = fmaf(ga[e].x, m, -pr), ei = fmaf(ga[e].y, m, -pi);
+            ga[e].x = pr + X.x;
+            ga[e].y = pi + X.y;
+            gl[e].x = fmaf(gl[e].x, m, er) + two_sum_err(pr, X.x);
+            gl[e].y = fmaf(gl[e].y, m, ei) + two_sum_err(pi, X.y);
+          }
+          continue;
+        }
         float kp = cf_pen * invw[kx];
         for (int u = 0; u < pw; ++u) kp *= (float)mx;
         if (gi == 0) {
           if (mj == 0) a0[e] = make_float2(kp * X.x, kp * X.y);
           else { a0[e].x = fmaf(kp, X.x, a0[e].x); a0[e].y = fmaf(kp, X.y, a0[e].y); }
-        } else if ((gi == 1 || gi == 4) && mj == 0) {
+        } else if (gi == first && mj == 0) {
           ga[e] = make_float2(kp * X.x, kp * X.y);
         } else {
           ga[e].x = fmaf(kp, X.x, ga[e].x);
           ga[e].y = fmaf(kp, X.y, ga[e].y);
         }
       }
-    const bool complete = (mj == M - 1) && (gi == 0 || gi == 3 || gi == 8);
+    // a multipole is complete after its last tile (for l = 6 its power-0 group)
+    const bool complete = (mj == M - 1) && (ELL == 6 ? gi == group_first(gi) : gi == group_last(gi));
     if (complete) {
-      const int slot = gi == 0 ? 0 : (gi == 3 ? 1 : 2);
-      float* wb = wbin + ((warp % nwb) * 3 + slot) * nbins;
-      float* wc = wb + nwb * 3 * nbins;
+      const int slot = gi == 0 ? 0 : (gi <= 3 ? 1 : (gi <= 8 ? 2 : 3));
+      if (ELL == 6 && slot > 0) {
 #pragma unroll
-      for (int q = 0; q < NBL; ++q)
+        for (int e = 0; e < E; ++e) {
+          const int kx = tl + (e / RL) * TPL + (e % RL) * (N / RL);
+          const float c = cf_pen * invw[kx];
+          ga[e] = make_float2(c * (ga[e].x + gl[e].x), c * (ga[e].y + gl[e].y));
+        }
+      }
+      float* wb = wbin + ((warp % nwb) * SLOTS + slot) * nbins;
+      float* wc = wb + nwb * SLOTS * nbins;
+      const float wgt = kz == 0 ? 1.f : 2.f;
+      // Half of the modes at a time: their sums first, so that the atomics' latencies
+      // overlap, then the rounding errors.
+      constexpr int EH = E / 2;
 #pragma unroll
-        for (int r = 0; r < RL; ++r) {
-          const int e = q * RL + r;
-          const int kx = tl + q * TPL + r * (N / RL);
+      for (int h = 0; h < 2; ++h) {
+        float val[EH], old[EH];
+#pragma unroll
+        for (int i = 0; i < EH; ++i) {
+          const int e = h * EH + i;
+          const int kx = tl + (e / RL) * TPL + (e % RL) * (N / RL);
           const int mx = kx <= N / 2 ? kx : kx - N;
-          const int n2 = mx * mx + ky * ky + kz * kz;
-          const int bin = (kz >= 0 && n2 < n2_hi) ? lut[n2] : -1;
-          if (bin >= 0) {
-            const float wgt = kz == 0 ? 1.f : 2.f;
-            float val;
-            if (slot == 0) {
-              val = wgt * (a0[e].x * a0[e].x + a0[e].y * a0[e].y);
-            } else {
-              const float inv = 1.f / (float)n2;
-              val = wgt * (slot == 1 ? inv : inv * inv) * (a0[e].x * ga[e].x + a0[e].y * ga[e].y);
-            }
-            add_compensated(wb + bin, wc + bin, val);
+          if (slot == 0) {
+            val[i] = wgt * (a0[e].x * a0[e].x + a0[e].y * a0[e].y);
+          } else {
+            const float inv = 1.f / (float)(mx * mx + ky * ky + kz * kz);
+            const float ik = slot == 1 ? inv : (slot == 2 ? inv * inv : inv * inv * inv);  // 1 / k^(2 slot)
+            val[i] = wgt * ik * (a0[e].x * ga[e].x + a0[e].y * ga[e].y);
           }
         }
+#pragma unroll
+        for (int i = 0; i < EH; ++i)
+          if (bins[h * EH + i] >= 0) old[i] = atomicAdd(wb + bins[h * EH + i], val[i]);
+#pragma unroll
+        for (int i = 0; i < EH; ++i)
+          if (bins[h * EH + i] >= 0) {
+            const float err = two_sum_err(old[i], val[i]);
+            if (err != 0.f) atomicAdd(wc + bins[h * EH + i], err);
+          }
+      }
     }
     __syncthreads();
   }
@@ -609,9 +677,9 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
     return;
   }
   // FP64 fold of every warp copy's sum and error term, once per CTA.
-  for (int b = tid; b < 3 * nbins; b += blockDim.x) {
+  for (int b = tid; b < SLOTS * nbins; b += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < nwb; ++w) v += (double)wbin[w * 3 * nbins + b] + (double)wcmp[w * 3 * nbins + b];
+    for (int w = 0; w < nwb; ++w) v += (double)wbin[w * SLOTS * nbins + b] + (double)wcmp[w * SLOTS * nbins + b];
     if (v != 0.0) atomicAdd(&acc[b], v);
   }
 }

@@ -42,6 +42,7 @@ struct Plan {
   cudaStream_t stream = nullptr;
   int n = 0, m = 1, ell = 0, kind = 2;
   int nb = 1, ng = 1;            // basis fields / k_x-power groups
+  int row_len = 0;               // doubles in a result row (result_row_len)
   double H = 0, kf = 0;
   Geom geom{};
   int ntiles = 0;
@@ -73,7 +74,7 @@ struct Plan {
   int* d_sync = nullptr;         // [2 m n + 2] per-plane counters, ticket, error flag
   float2* d_g = nullptr;         // [m][ng][n][np_pad] grouped y,z transforms
   CUtensorMap gmap;              // 2D tensor map of d_g for the x-stage TMA loads
-  double* d_acc = nullptr;       // [3][n_bins] shell sums
+  double* d_acc = nullptr;       // [4][n_bins] shell sums (slot 3 for l_max = 6)
   double* d_sums = nullptr;      // [SUM_COUNT]
   double* d_result = nullptr;    // [5 n_bins + 3]
   unsigned* d_tile_count = nullptr;  // [ntiles]
@@ -130,6 +131,8 @@ __host__ __device__ constexpr int x_box_rows(int n) {
   return n <= 256 ? n : (n % 256 == 0 ? 256 : (n % 192 == 0 ? 192 : 128));
 }
 ys_status ensure_particles(Plan& p, int64_t total);
+// Doubles in a result row: 5 n_bins + 5, plus n_bins of P_6 for l_max = 6.
+inline int result_row_len(int nbins, int ell) { return 5 * nbins + 5 + (ell >= 6 ? nbins : 0); }
 extern thread_local std::string g_last_cuda_error;
 cudaError_t launch_measure(Plan& p);
 ys_status assign_noalloc(Plan& p, const ys_catalog& gal, const ys_catalog& ran, std::string& why);

@@ -62,6 +62,7 @@ class YsResult(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("norm_I", ctypes.c_double),
         ("shot_noise", ctypes.c_double),
+        ("p6", ctypes.c_void_p),
     ]
 
 
@@ -133,6 +134,9 @@ def _lib():
         lib.ys_mlp_correct.argtypes = [P, P, ctypes.c_int32, I64, ctypes.c_int32, ctypes.c_double, P, P]
         lib.ys_mlp_destroy.argtypes = [P]
         lib.ys_wedges.argtypes = [P, ctypes.c_int32, I64, ctypes.c_int32, P, P]
+        lib.ys_sum_gal.argtypes = [ctypes.POINTER(YsConfig), ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog),
+                                   P, P]
+        lib.ys_sum_grid.argtypes = [P, P, P]
         lib.ys_status_string.argtypes = [ctypes.c_int]
         lib.ys_status_string.restype = ctypes.c_char_p
         lib.ys_last_cuda_error.restype = ctypes.c_char_p
@@ -143,7 +147,7 @@ def _lib():
                      "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy",
                      "ys_mlp_create", "ys_mlp_get_state", "ys_mlp_set_state", "ys_mlp_forward",
                      "ys_mlp_gradient", "ys_mlp_train_step", "ys_mlp_features", "ys_mlp_correct",
-                     "ys_mlp_destroy", "ys_wedges"):
+                     "ys_mlp_destroy", "ys_wedges", "ys_sum_gal", "ys_sum_grid"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -172,6 +176,7 @@ class Result:
     norm_I: float
     shot_noise: float
     status: int = YS_OK
+    p6: np.ndarray | None = None   # l_max = 6 plans only
 
 
 def _check(status, where, allow=()):
@@ -213,13 +218,19 @@ def make_config(n_mesh, box_min, box_len, observer=(0.0, 0.0, 0.0), assign="cic"
     return cfg
 
 
-def parse_row(row, n_bins):
-    """Split one result row [k | n_modes | p0 | p2 | p4 | alpha, I, S/I, n_out, timeout]."""
+def row_len(n_bins, ell_max=4):
+    """Doubles in a result row: 5 n_bins + 5, plus n_bins of P_6 for l_max = 6."""
+    return 5 * n_bins + 5 + (n_bins if ell_max >= 6 else 0)
+
+
+def parse_row(row, n_bins, ell_max=4):
+    """Split one result row [k | n_modes | p0 | p2 | p4 | alpha, I, S/I, n_out, timeout (| p6)]."""
     row = np.asarray(row, dtype=np.float64)
     nb = n_bins
+    p6 = row[5 * nb + 5:6 * nb + 5].copy() if ell_max >= 6 else None
     return Result(row[:nb], row[nb:2 * nb], row[2 * nb:3 * nb], row[3 * nb:4 * nb], row[4 * nb:5 * nb],
                   float(row[5 * nb]), float(row[5 * nb + 1]), float(row[5 * nb + 2]),
-                  YS_ERR_TIMEOUT if row[5 * nb + 4] != 0 else (YS_ERR_ARG if row[5 * nb + 3] > 0 else YS_OK))
+                  YS_ERR_TIMEOUT if row[5 * nb + 4] != 0 else (YS_ERR_ARG if row[5 * nb + 3] > 0 else YS_OK), p6)
 
 
 class Plan:
@@ -234,6 +245,8 @@ class Plan:
         n_bins = cfg.n_bins
         self.cfg = cfg
         self.n_bins = n_bins
+        self.ell_max = ell_max
+        self.row_len = row_len(n_bins, ell_max)
         h = ctypes.c_void_p()
         _check(lib.ys_plan_create(ctypes.byref(cfg), ctypes.byref(h)), "ys_plan_create")
         self._h = h
@@ -262,16 +275,20 @@ class Plan:
 
     def _result_struct(self):
         nb = self.n_bins
-        arrs = [np.empty(nb, dtype=np.float64) for _ in range(5)]
+        arrs = [np.empty(nb, dtype=np.float64) for _ in range(6)]
         res = YsResult()
-        res.k_mean, res.n_modes, res.p0, res.p2, res.p4 = [a.ctypes.data for a in arrs]
+        res.k_mean, res.n_modes, res.p0, res.p2, res.p4, res.p6 = [a.ctypes.data for a in arrs]
         return res, arrs
+
+    def _result(self, res, arrs, st):
+        return Result(*arrs[:5], res.alpha, res.norm_I, res.shot_noise, st,
+                      arrs[5] if self.ell_max >= 6 else None)
 
     def measure(self, allow_outside=False):
         res, arrs = self._result_struct()
         st = _check(_lib().ys_measure_multipoles(self._h, ctypes.byref(res)), "ys_measure_multipoles",
                     allow=(YS_ERR_ARG,) if allow_outside else ())
-        return Result(*arrs, res.alpha, res.norm_I, res.shot_noise, st)
+        return self._result(res, arrs, st)
 
     def estimate_host(self, gal, ran):
         """End to end from host numpy float32 arrays (x, y, z, w, nbar)."""
@@ -282,7 +299,7 @@ class Plan:
         res, arrs = self._result_struct()
         st = _check(_lib().ys_estimate_host(self._h, ctypes.byref(g), ctypes.byref(r), ctypes.byref(res)),
                     "ys_estimate_host")
-        return Result(*arrs, res.alpha, res.norm_I, res.shot_noise, st)
+        return self._result(res, arrs, st)
 
     def autotune(self, gal, ran, reps=3):
         """ys_plan_autotune on device catalogues; returns the chosen YsTuning."""
@@ -291,6 +308,19 @@ class Plan:
         _check(_lib().ys_plan_autotune(self._h, ctypes.byref(g), ctypes.byref(r), reps, ctypes.byref(t)),
                "ys_plan_autotune")
         return t
+
+    def sum_grid(self, wedges=False):
+        """ys_sum_grid: the direct sum over this plan's assigned mesh nodes.  Returns the
+        Result, and (P_perp, P_para) of the wedges' definition when ``wedges``."""
+        import torch
+        row = torch.empty(self.row_len, dtype=torch.float64, device="cuda")
+        wd = torch.empty(2 * self.n_bins, dtype=torch.float64, device="cuda") if wedges else None
+        _check(_lib().ys_sum_grid(self._h, _ptr(row), _ptr(wd)), "ys_sum_grid")
+        res = parse_row(row.cpu().numpy(), self.n_bins, self.ell_max)
+        if not wedges:
+            return res
+        w = wd.cpu().numpy()
+        return res, (w[:self.n_bins], w[self.n_bins:])
 
     def set_fault_injection(self, wait_limit_ns=0, skip_plane=-1):
         """ys_plan_set_fault_injection: bound of the y,z-stage waits, and the plane whose
@@ -337,6 +367,7 @@ class Batch:
         self._h = h
         self.n = n
         self.n_bins = [c.n_bins for c in configs]
+        self.ell_max = [c.ell_max for c in configs]
         self.stride = int(lib.ys_batch_result_stride(h))
         self._keep = None
 
@@ -358,7 +389,7 @@ class Batch:
 
     def results(self, d_results):
         host = d_results.cpu().numpy() if hasattr(d_results, "cpu") else np.asarray(d_results)
-        return [parse_row(host[i], self.n_bins[i]) for i in range(self.n)]
+        return [parse_row(host[i], self.n_bins[i], self.ell_max[i]) for i in range(self.n)]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -461,3 +492,24 @@ def wedges(d_rows, n_bins, d_out, stream=None):
     float64 (n_cat, stride)) into d_out (device float64 (n_cat, 2, n_bins))."""
     n_cat, stride = d_rows.shape
     _check(_lib().ys_wedges(_ptr(d_rows), n_cat, stride, n_bins, _ptr(d_out), stream), "ys_wedges")
+
+
+def sum_gal(n_mesh, box_min, box_len, gal, ran, observer=(0.0, 0.0, 0.0), ell_max=4, k_min=0.0, dk=0.01,
+            n_bins=None, k_max=None, alpha=-1.0, wedges=False, stream=None):
+    """ys_sum_gal: the galaxy direct sum at the half-grid modes of an n_mesh^3 lattice.
+    gal, ran: tuples of device float32 tensors (x, y, z, w, nbar).  Returns the Result,
+    and (P_perp, P_para) of the wedges' definition when ``wedges``."""
+    import torch
+    cfg = make_config(n_mesh, box_min, box_len, observer, "cic", False, False, ell_max, k_min, dk, n_bins,
+                      k_max, alpha, 0, stream)
+    nb = cfg.n_bins
+    row = torch.empty(row_len(nb, ell_max), dtype=torch.float64, device="cuda")
+    wd = torch.empty(2 * nb, dtype=torch.float64, device="cuda") if wedges else None
+    g, r = Plan._cat(*gal), Plan._cat(*ran)
+    _check(_lib().ys_sum_gal(ctypes.byref(cfg), ctypes.byref(g), ctypes.byref(r), _ptr(row), _ptr(wd)),
+           "ys_sum_gal")
+    res = parse_row(row.cpu().numpy(), nb, ell_max)
+    if not wedges:
+        return res
+    w = wd.cpu().numpy()
+    return res, (w[:nb], w[nb:])

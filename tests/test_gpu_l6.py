@@ -1,0 +1,127 @@
+"""l_max = 6 on the GPU (through the C ABI) against the FP64 oracle, shell by shell.
+
+The paper notes after Eq. (13) that higher orders follow from the same
+decomposition; the oracle carries it literally (the 28 degree-6 fields,
+``oracle.terms.A6_TERMS``) and P_6 = 13/I <Re A_0 A_6^*>.  The bar is the one
+of every parity test: |P_l^gpu - P_l^oracle| <= 1e-4 |P_l^oracle| wherever
+|P_l| > 1e-2 of the raw monopole.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.binning import BinSpec
+
+torch = pytest.importorskip("torch")
+ys = pytest.importorskip("paper_1505_05341_gb300")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def to_dev(cat):
+    return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (cat.x, cat.y, cat.z, cat.w, cat.nbar))
+
+
+def run_gpu(gal, ran, geo, n, bins, assign, interlace, compensate=True, ell=6):
+    with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign=assign, interlace=interlace,
+                 compensate=compensate, ell_max=ell, k_min=bins.k_min, dk=bins.dk, n_bins=bins.n_bins,
+                 stream=torch.cuda.current_stream().cuda_stream) as plan:
+        plan.assign(to_dev(gal), to_dev(ran))
+        return plan.measure()
+
+
+def compare6(res, ref, label):
+    nm = ref.n_modes
+    assert np.array_equal(res.n_modes, nm), label
+    has = nm > 0
+    raw = np.where(has, ref.sum0 / np.where(has, nm, 1) / ref.norm.I, 0.0)
+    worst = {}
+    for l in (0, 2, 4, 6):
+        g, o = getattr(res, f"p{l}"), getattr(ref, f"p{l}")
+        assert g is not None and o is not None
+        assert np.all(np.isnan(g[~has]))
+        sel = has & (np.abs(o) > 1e-2 * raw)
+        assert sel.any(), (label, l)
+        rel = np.abs(g[sel] - o[sel]) / np.abs(o[sel])
+        worst[l] = float(rel.max())
+        assert rel.max() <= TOL, (label, l, rel.max(), np.nonzero(sel)[0][np.argmax(rel)])
+    print(f"{label}: worst rel err per multipole {worst}")
+    return worst
+
+
+def test_l6_ngp_on_nodes_matches_galaxy_sum():
+    """Particles on nodes + NGP + no window: GPU = oracle galaxy sum for l <= 6."""
+    n = 16
+    gal, ran, geo = synth.on_node_catalog(n, (64.0, 32.0, 96.0), 128.0, 300, 1500, seed=3)
+    bins = BinSpec(0.0, 0.02, 20)
+    ref = oracle.sum_gal(gal, ran, geo, n, bins, ell_max=6)
+    res = run_gpu(gal, ran, geo, n, bins, "ngp", False, compensate=False)
+    compare6(res, ref, "l6_ngp_on_nodes")
+
+
+@pytest.mark.parametrize("n,kind,interlace", [
+    (32, "cic", False),
+    (64, "tsc", True),
+    (96, "cic", True),
+    (192, "tsc", False),
+])
+def test_l6_observer_centred_box(n, kind, interlace):
+    """Box centred on the observer (LOS in every octant), radix-3 meshes included."""
+    gal, ran, geo = synth.poisson_cube(20_000, 100_000, side=1000.0, center=(0.0, 0.0, 0.0), seed=n + 6)
+    bins = BinSpec.up_to(0.9 * np.pi * n / geo.box_len, 0.007)
+    ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign=kind, interlace=interlace, ell_max=6)
+    res = run_gpu(gal, ran, geo, n, bins, kind, interlace)
+    compare6(res, ref, f"l6_centred_{n}_{kind}_{interlace}")
+
+
+def test_l6_clustered_cube_tsc_interlaced():
+    """Clustered redshift-space cube (Zel'dovich + radial RSD), 128^3 TSC interlaced."""
+    gal, ran, geo = synth.zeldovich_cube(150_000, 750_000, seed=12)
+    bins = BinSpec.up_to(np.pi * 128 / geo.box_len, 0.01)
+    ref = oracle.fft_multipoles(gal, ran, geo, 128, bins, assign="tsc", interlace=True, ell_max=6)
+    res = run_gpu(gal, ran, geo, 128, bins, "tsc", True)
+    compare6(res, ref, "l6_zeldovich_cube128")
+
+
+def test_l6_cone_mock_256():
+    """The clustered cone mock (1e6 + 5e6, FKP weights), 256^3 TSC interlaced, l <= 6."""
+    gal, ran, geo, _ = synth.workload("cone256_tsc_il")
+    bins = BinSpec.up_to(np.pi * 256 / geo.box_len, 0.01)
+    ref = oracle.fft_multipoles(gal, ran, geo, 256, bins, assign="tsc", interlace=True, ell_max=6)
+    res = run_gpu(gal, ran, geo, 256, bins, "tsc", True)
+    compare6(res, ref, "l6_cone256")
+
+
+def test_l6_leaves_lower_multipoles_alone():
+    """An l_max = 6 plan gives the l <= 4 multipoles of an l_max = 4 plan (both float
+    evaluations, so twice the bar), and its P_6 rows sit after the five scalars."""
+    gal, ran, geo = synth.poisson_cube(20_000, 100_000, side=800.0, center=(300.0, 200.0, 100.0), seed=61)
+    n = 64
+    bins = BinSpec.up_to(np.pi * n / geo.box_len, 0.01)
+    r6 = run_gpu(gal, ran, geo, n, bins, "tsc", True, ell=6)
+    r4 = run_gpu(gal, ran, geo, n, bins, "tsc", True, ell=4)
+    assert r4.p6 is None and r6.p6 is not None
+    has = r4.n_modes > 0
+    raw = r4.p0 + r4.shot_noise
+    for l in (0, 2, 4):
+        a, b = getattr(r4, f"p{l}"), getattr(r6, f"p{l}")
+        sel = has & (np.abs(a) > 1e-2 * raw)
+        assert np.max(np.abs(a[sel] - b[sel]) / np.abs(a[sel])) <= 2 * TOL
+    with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, ell_max=6,
+                 dk=bins.dk, n_bins=bins.n_bins, stream=torch.cuda.current_stream().cuda_stream) as plan:
+        plan.assign(to_dev(gal), to_dev(ran))
+        row = torch.empty(plan.row_len, dtype=torch.float64, device="cuda")
+        plan.measure_async(row)
+        torch.cuda.synchronize()
+        parsed = ys.parse_row(row.cpu().numpy(), bins.n_bins, 6)
+    sel = has & (np.abs(r6.p6) > 1e-2 * raw)   # two float evaluations: twice the bar
+    assert np.max(np.abs(parsed.p6[sel] - r6.p6[sel]) / np.abs(r6.p6[sel])) <= 2 * TOL
+
+
+def test_l6_refused_above_512():
+    with pytest.raises(ys.YstatError) as ei:
+        ys.Plan(768, (0.0, 0.0, 0.0), 1000.0, assign="cic", ell_max=6, dk=0.01, n_bins=10)
+    assert ei.value.status == ys.ystat.YS_ERR_UNSUPPORTED
