@@ -461,6 +461,11 @@ def run_ours(args):
             line["cufft_comparison"] = cmp_
         except Exception as exc:  # a comparison only: never fail the benchmark for it
             line["cufft_comparison"] = {"error": str(exc)[:200]}
+    if world == 1 and not args.no_extras and args.workload == WORKLOAD:
+        try:
+            line["extras"] = run_extras(gal, ran, geo, dgal, dran, n_bins, max(3, min(args.steps, 5)))
+        except Exception as exc:  # sub-entries only: never fail the benchmark for them
+            line["extras"] = {"error": str(exc)[:300]}
     if world == 1 and not args.no_batched and args.workload == WORKLOAD:
         del dgal, dran
         plan.close()
@@ -487,6 +492,131 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _event_time_s(fn, steps, stream):
+    """Seconds per call of fn (queued on stream), by CUDA events after one warm-up."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / steps
+
+
+def run_extras(gal, ran, geo, dgal, dran, n_bins, steps):
+    """Sub-entries for the rows beyond l <= 4 on the survey catalogue: l_max = 6, shared
+    randoms, the direct galaxy sum and the wedges' definition (Sec. 4, 5), and the
+    paper-shaped mock on the meshes of Table 1.  Each is timed with CUDA events on
+    device-resident inputs; none is the headline metric."""
+    import torch
+
+    import paper_1505_05341_gb300 as ys
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    out = {}
+
+    # l <= 6 on the same 512^3 TSC interlaced survey catalogue (28 more fields)
+    with ys.Plan(N_MESH, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, ell_max=6,
+                 dk=DK, n_bins=n_bins, max_particles=gal.n + ran.n, stream=sp) as p6:
+        row = torch.empty(p6.row_len, dtype=torch.float64, device="cuda")
+        t = _event_time_s(lambda: (p6.assign(dgal, dran), p6.measure_async(row)), steps, stream)
+        out["l6"] = {"value": 1.0 / t, "unit": UNIT, "ms_per_catalogue": 1e3 * t, "fields": "1+6+15+28",
+                     "what": "ys_assign + ys_measure_multipoles_async with ell_max = 6, 512^3 TSC interlaced, "
+                             "1e7 + 5e7, shells to 0.4"}
+    torch.cuda.empty_cache()
+
+    # shared randoms: the 5e7 randoms deposited once, each catalogue's 1e7 galaxies after
+    with ys.Plan(N_MESH, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, ell_max=4,
+                 dk=DK, n_bins=n_bins, max_particles=gal.n + ran.n, stream=sp) as pc:
+        row = torch.empty(pc.row_len, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        pc.cache_randoms(dran)
+        torch.cuda.synchronize()
+        t_cache = time.perf_counter() - t0
+        t = _event_time_s(lambda: (pc.assign_cached(dgal), pc.measure_async(row)), steps, stream)
+        out["shared_randoms"] = {"value": 1.0 / t, "unit": UNIT, "ms_per_catalogue": 1e3 * t,
+                                 "cache_ms_once": 1e3 * t_cache,
+                                 "what": "ys_assign_cached (1e7 galaxies against 5e7 kept randoms) + "
+                                         "ys_measure_multipoles_async, 512^3 TSC interlaced"}
+    torch.cuda.empty_cache()
+
+    # the direct galaxy sum on the GPU: its rate, and the paper's comparison (Sec. 4: the
+    # FFT method is > 1000x faster than the sums) on this catalogue
+    import synth
+    from oracle.binning import BinSpec
+    cg, cr, cgeo, _ = synth.workload("cube32_cic")
+    cbins = BinSpec.up_to(math.pi * 32 / cgeo.box_len, 0.01)
+    dev = lambda c: tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (c.x, c.y, c.z, c.w, c.nbar))
+    dcg, dcr = dev(cg), dev(cr)
+    sg = lambda: ys.sum_gal(32, cgeo.box_min, cgeo.box_len, dcg, dcr, observer=cgeo.observer, dk=cbins.dk,
+                            n_bins=cbins.n_bins, stream=sp)
+    sg()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        sg()
+    t_sg = (time.perf_counter() - t0) / 3
+    terms = (cg.n + cr.n) * half_modes_below(math.pi * 32 / cgeo.box_len, cgeo.box_len, 32)
+    rate = terms / t_sg
+    survey_terms = (gal.n + ran.n) * half_modes_below(K_MAX, geo.box_len, N_MESH)
+    out["sum_gal"] = {"terms_per_s": rate, "s_per_c1_catalogue": t_sg,
+                      "survey_terms": survey_terms, "survey_s_extrapolated": survey_terms / rate,
+                      "what": "ys_sum_gal (l <= 4) on the 2000 + 10000-point cube, 32^3 lattice, synchronous "
+                              "call; extrapolated by terms to the 512^3 survey catalogue for the FFT-vs-sum ratio"}
+
+    # Fig. 2's comparison: wedges by their definition against Eqs. 16-17, four mocks
+    gaps_perp, gaps_para = [], []
+    for seed in (301, 302, 303, 304):
+        wg, wr, wgeo = synth.zeldovich_cube(20_000, 100_000, n_lattice=64, seed=seed)
+        n = 32
+        wb = BinSpec.up_to(math.pi * n / wgeo.box_len, 0.02)
+        dwg, dwr = dev(wg), dev(wr)
+        res, (pp, pq) = ys.sum_gal(n, wgeo.box_min, wgeo.box_len, dwg, dwr, observer=wgeo.observer, dk=wb.dk,
+                                   n_bins=wb.n_bins, wedges=True, stream=sp)
+        with ys.Plan(n, wgeo.box_min, wgeo.box_len, wgeo.observer, assign="tsc", interlace=True, ell_max=4,
+                     dk=wb.dk, n_bins=wb.n_bins, stream=sp) as pw:
+            pw.assign(dwg, dwr)
+            rowd = torch.empty((1, pw.row_len), dtype=torch.float64, device="cuda")
+            pw.measure_async(rowd[0])
+            wout = torch.empty((1, 2, wb.n_bins), dtype=torch.float64, device="cuda")
+            ys.wedges(rowd, wb.n_bins, wout, stream=sp)
+            torch.cuda.synchronize()
+            approx = wout.cpu().numpy()[0]
+        k = res.k
+        sel = (res.n_modes > 0) & (k > 0.05) & (k < 0.2)
+        raw = res.p0[sel] + res.shot_noise   # the monopole before shot noise: P_perp can cross zero
+        gaps_perp.append(np.abs(approx[0][sel] - pp[sel]) / raw)
+        gaps_para.append(np.abs(approx[1][sel] - pq[sel]) / raw)
+    out["wedges_definition_vs_eqs16_17"] = {
+        "mean_gap_perp_over_raw_p0": float(np.mean(np.concatenate(gaps_perp))),
+        "mean_gap_para_over_raw_p0": float(np.mean(np.concatenate(gaps_para))),
+        "what": "Sec. 5 / Fig. 2 on synthetic mocks: P_perp, P_para by their definition (GPU galaxy sum, "
+                "top hats at |mu| = 1/2) against Eqs. 16-17 from the GPU FFT multipoles (32^3 TSC interlaced); "
+                "mean |gap| / (P_0 + S/I) over shells 0.05 < k < 0.2 h/Mpc of four 20 000-galaxy Zel'dovich cubes"}
+    torch.cuda.empty_cache()
+
+    # the paper-shaped mock (525 000 galaxies, 10x randoms, CIC) on Table 1's meshes
+    pg, pr, pgeo, _ = synth.workload("paper512_cic")
+    dpg, dpr = dev(pg), dev(pr)
+    shaped = {}
+    for n in (512, 1024):
+        nb = int(math.ceil(math.pi * n / pgeo.box_len / DK - 1e-9))
+        with ys.Plan(n, pgeo.box_min, pgeo.box_len, pgeo.observer, assign="cic", interlace=False, ell_max=4,
+                     dk=DK, n_bins=nb, max_particles=pg.n + pr.n, stream=sp) as pp_:
+            row = torch.empty(pp_.row_len, dtype=torch.float64, device="cuda")
+            t = _event_time_s(lambda: (pp_.assign(dpg, dpr), pp_.measure_async(row)), max(2, steps - 2), stream)
+            shaped[str(n)] = {"value": 1.0 / t, "unit": UNIT, "s_per_catalogue": t,
+                              "paper_s_per_catalogue": {512: 72.0, 1024: 450.0}[n]}
+        torch.cuda.empty_cache()
+    out["paper_shaped"] = {"meshes": shaped, "what": "paper512_cic / paper1024_cic: 525 000 Zel'dovich galaxies, "
+                           "5.25e6 randoms, 3500 Mpc/h box, CIC, shells of 0.01 to Nyquist; the paper's times "
+                           "(Table 1, 16 CPU cores, its own PTHalos mock) are context only"}
+    return out
 
 
 def batched_catalogues(n_cat=256, first_seed=1000):
@@ -699,6 +829,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -129,6 +129,22 @@ size_t ys_plan_device_bytes(const ys_plan* plan);
  * reported by the next ys_measure_multipoles as YS_ERR_ARG. */
 ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran);
 
+/* Shared randoms.  Sec. 4 notes that catalogues which share one random catalogue
+ * (mocks measured against the same randoms) need it processed only once.
+ * ys_randoms_cache deposits ran (DEVICE pointers) once, with weight +w, into a
+ * plan-owned copy of the mesh(es) -- an extra m n_mesh^3 floats, allocated on the
+ * first call -- and keeps the FP64 sums sum w, sum w^2, sum w^2 nbar.  It overwrites
+ * the plan's current assignment (call ys_assign or ys_assign_cached again before
+ * measuring).  Asynchronous. */
+ys_status ys_randoms_cache(ys_plan* plan, const ys_catalog* ran);
+
+/* Eq. (1) against the kept randoms: deposits gal (DEVICE pointers) only and writes
+ * F = (galaxy deposit) - alpha (kept random deposit), alpha = sum_gal w / sum_ran w
+ * (or cfg.alpha) formed on the device, with the catalogue sums of I and S completed
+ * from the kept ones.  The result equals ys_assign with the same randoms up to float
+ * rounding.  YS_ERR_STATE without a ys_randoms_cache.  Asynchronous. */
+ys_status ys_assign_cached(ys_plan* plan, const ys_catalog* gal);
+
 /* Eqs. (4)-(13): the LOS-weighted fields, their FFTs, the k-space combination,
  * the shell sums and Eqs. (6)-(8).  Writes the device result row
  *   d_out[0 .. 5 n_bins + 5) = [k_mean | n_modes | p0 | p2 | p4 |

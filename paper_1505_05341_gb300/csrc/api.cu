@@ -59,6 +59,7 @@ void free_all(Plan& p) {
   dfree(p.d_mesh); dfree(p.d_z); dfree(p.d_sync); dfree(p.d_g); dfree(p.d_acc); dfree(p.d_sums); dfree(p.d_result);
   dfree(p.d_tile_count); dfree(p.d_tile_off); dfree(p.d_tile_cur); dfree(p.d_rec);
   dfree(p.d_stage);
+  dfree(p.d_rmesh); dfree(p.d_rsums);
   p.device_bytes = 0;
 }
 
@@ -556,6 +557,42 @@ ys_status ys_assign(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran)
   ys_status st = ys::ensure_particles(p, gal->n + ran->n);
   if (st != YS_OK) return st;
   cudaError_t e = ys::launch_assign(p, *gal, *ran);
+  if (e) return ys::cuda_fail(e);
+  p.assigned = true;
+  return YS_OK;
+}
+
+ys_status ys_randoms_cache(ys_plan* plan, const ys_catalog* ran) {
+  if (!plan || !ys::catalog_ok(ran)) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  ys_status st = ys::ensure_particles(p, ran->n);
+  if (st != YS_OK) return st;
+  cudaError_t e;
+  const size_t n3 = (size_t)p.n * p.n * p.n;
+  if (!p.d_rmesh && ((e = ys::dalloc(p, p.d_rmesh, p.m * n3)) || (e = ys::dalloc(p, p.d_rsums, 3))))
+    return ys::cuda_fail(e);
+  // The randoms go through the assignment as a catalogue of weight +w, into the kept
+  // mesh instead of the plan's; their FP64 sums are taken separately.
+  const ys_catalog none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  float* mesh = p.d_mesh;
+  p.d_mesh = p.d_rmesh;
+  e = ys::launch_assign(p, *ran, none);
+  p.d_mesh = mesh;
+  if (!e) e = ys::launch_random_sums(p, *ran, p.d_rsums);
+  if (e) return ys::cuda_fail(e);
+  p.randoms_cached = true;
+  p.assigned = false;  // the plan's catalogue sums were used as scratch
+  return YS_OK;
+}
+
+ys_status ys_assign_cached(ys_plan* plan, const ys_catalog* gal) {
+  if (!plan || !ys::catalog_ok(gal)) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  if (!p.randoms_cached) return YS_ERR_STATE;
+  ys_status st = ys::ensure_particles(p, gal->n);
+  if (st != YS_OK) return st;
+  const ys_catalog none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  cudaError_t e = ys::launch_assign(p, *gal, none, p.d_rmesh, p.d_rsums);
   if (e) return ys::cuda_fail(e);
   p.assigned = true;
   return YS_OK;

@@ -256,10 +256,13 @@ k_scan(const unsigned* __restrict__ count, int ntiles, unsigned* __restrict__ of
   if (t == 1023) off[ntiles] = part[1023];
 }
 
+// rmesh (shared randoms): the kept random mesh sum_ran w W, written as
+// F = (galaxy deposit) - alpha rmesh, with alpha from the catalogue sums.
 template <int KIND, int M>
 __global__ void __launch_bounds__(THREADS)
 k_deposit(Geom g, const float2* __restrict__ nodes, const unsigned* __restrict__ off,
-          const float4* __restrict__ rec, float* __restrict__ mesh) {
+          const float4* __restrict__ rec, float* __restrict__ mesh, const float* __restrict__ rmesh,
+          const double* __restrict__ sums, double alpha_cfg) {
   extern __shared__ float s_tile[];
   const int n = g.n;
   const int tdx = g.tdim[0], tdy = g.tdim[1], tdz = g.tdim[2];
@@ -314,22 +317,50 @@ k_deposit(Geom g, const float2* __restrict__ nodes, const unsigned* __restrict__
   }
   __syncthreads();
   const size_t n3 = (size_t)n * n * n;
+  const float ran_scale =
+      rmesh ? (float)(-(alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR])) : 0.f;
   for (int k = threadIdx.x; k < M * tvol; k += blockDim.x) {
     const int mj = k / tvol;
     const int rr = k - mj * tvol;
     const int lz = rr % tdz;
     const int ly = (rr / tdz) % tdy;
     const int lx = rr / (tdz * tdy);
-    mesh[mj * n3 + ((size_t)(o[0] + lx) * n + (o[1] + ly)) * n + (o[2] + lz)] = s_tile[k];
+    const size_t at = mj * n3 + ((size_t)(o[0] + lx) * n + (o[1] + ly)) * n + (o[2] + lz);
+    mesh[at] = rmesh ? fmaf(ran_scale, rmesh[at], s_tile[k]) : s_tile[k];
   }
 }
 
+// FP64 sums of a random catalogue (sum w, sum w^2, sum w^2 nbar) for the kept copy.
+__global__ void k_ran_sums(const float* __restrict__ w, const float* __restrict__ nbar, int64_t n,
+                           double* __restrict__ out) {
+  double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w ? (double)w[i] : 1.0;
+    s1 += v;
+    s2 += v * v;
+    if (nbar) s3 += v * v * (double)nbar[i];
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  s3 = warp_sum(s3);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], s1);
+    atomicAdd(&out[1], s2);
+    atomicAdd(&out[2], s3);
+  }
+}
+
+// rmesh != nullptr (shared randoms): ran is empty, the random sums come from rsums
+// (sum w, sum w^2, sum w^2 nbar) and the deposit subtracts alpha rmesh.
 template <int KIND, int M>
-cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
+cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, const float* rmesh = nullptr,
+                       const double* rsums = nullptr) {
   cudaStream_t st = p.stream;
   cudaError_t err;
   if ((err = cudaMemsetAsync(p.d_tile_count, 0, sizeof(unsigned) * p.ntiles, st)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(p.d_sums, 0, sizeof(double) * SUM_COUNT, st)) != cudaSuccess) return err;
+  if (rsums && (err = cudaMemcpyAsync(p.d_sums + SUM_WR, rsums, sizeof(double) * 3, cudaMemcpyDeviceToDevice, st)))
+    return err;
   auto blocks = [](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + THREADS - 1) / THREADS, 152 * 16)); };
   const ys_catalog* cats[2] = {&gal, &ran};
   // counting: shared-memory histograms while the tile counters fit (a few CTAs per SM)
@@ -385,23 +416,33 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
       cudaSuccess)
     return err;
   LaunchScope ls(p, 3);
-  k_deposit<KIND, M><<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_nodes, p.d_tile_off, p.d_rec, p.d_mesh);
+  k_deposit<KIND, M><<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_nodes, p.d_tile_off, p.d_rec, p.d_mesh, rmesh,
+                                                       p.d_sums, p.cfg.alpha);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
+cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, const float* rmesh,
+                          const double* rsums) {
   const int key = p.kind * 2 + (p.m - 1);
   switch (key) {
-    case 2: return run_assign<1, 1>(p, gal, ran);
-    case 3: return run_assign<1, 2>(p, gal, ran);
-    case 4: return run_assign<2, 1>(p, gal, ran);
-    case 5: return run_assign<2, 2>(p, gal, ran);
-    case 6: return run_assign<3, 1>(p, gal, ran);
-    case 7: return run_assign<3, 2>(p, gal, ran);
+    case 2: return run_assign<1, 1>(p, gal, ran, rmesh, rsums);
+    case 3: return run_assign<1, 2>(p, gal, ran, rmesh, rsums);
+    case 4: return run_assign<2, 1>(p, gal, ran, rmesh, rsums);
+    case 5: return run_assign<2, 2>(p, gal, ran, rmesh, rsums);
+    case 6: return run_assign<3, 1>(p, gal, ran, rmesh, rsums);
+    case 7: return run_assign<3, 2>(p, gal, ran, rmesh, rsums);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_random_sums(Plan& p, const ys_catalog& ran, double* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 3, p.stream);
+  if (e || ran.n == 0) return e;
+  const unsigned blocks = (unsigned)std::min<int64_t>(152 * 8, (ran.n + THREADS - 1) / THREADS);
+  k_ran_sums<<<blocks, THREADS, 0, p.stream>>>(ran.w, ran.nbar, ran.n, out);
+  return cudaGetLastError();
 }
 
 }  // namespace ys

@@ -81,6 +81,10 @@ struct Plan {
   unsigned* d_tile_off = nullptr;    // [ntiles + 1]
   unsigned* d_tile_cur = nullptr;    // [ntiles]
   float4* d_rec = nullptr;       // [rec_cap] (x, y, z, signed weight) per (particle, tile)
+  // shared randoms (ys_randoms_cache): sum_ran w W per mesh node, and its FP64 sums
+  float* d_rmesh = nullptr;      // [m][n][n][n]
+  double* d_rsums = nullptr;     // [3] sum w, sum w^2, sum w^2 nbar
+  bool randoms_cached = false;
   int64_t rec_cap = 0;
   int64_t part_cap = 0;
   // host staging for ys_estimate_host
@@ -118,7 +122,11 @@ struct LaunchScope {
 };
 
 // Kernel launchers (return cudaError_t of the launch).
-cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran);
+// rmesh / rsums: shared randoms (ys_assign_cached); nullptr for a plain assignment.
+cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, const float* rmesh = nullptr,
+                          const double* rsums = nullptr);
+// FP64 sum w, sum w^2, sum w^2 nbar of a random catalogue into out[3].
+cudaError_t launch_random_sums(Plan& p, const ys_catalog& ran, double* out);
 // Scatter tile shape (nodes per axis, capped at N); updates geom and ntiles.
 void set_tiles(Plan& p, int tx, int ty, int tz);
 // y,z grid size; updates the ring lead D and slots S (S never exceeds the allocation).

@@ -111,6 +111,8 @@ def _lib():
                                          ctypes.POINTER(YsResult)]
         lib.ys_plan_destroy.argtypes = [P]
         lib.ys_assign_noalloc.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog)]
+        lib.ys_randoms_cache.argtypes = [P, ctypes.POINTER(YsCatalog)]
+        lib.ys_assign_cached.argtypes = [P, ctypes.POINTER(YsCatalog)]
         lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
         lib.ys_plan_set_fault_injection.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
         lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
@@ -143,7 +145,7 @@ def _lib():
         for name in ("ys_plan_create", "ys_assign", "ys_measure_multipoles_async",
                      "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
                      "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc", "ys_plan_autotune",
-                     "ys_plan_set_fault_injection",
+                     "ys_plan_set_fault_injection", "ys_randoms_cache", "ys_assign_cached",
                      "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy",
                      "ys_mlp_create", "ys_mlp_get_state", "ys_mlp_set_state", "ys_mlp_forward",
                      "ys_mlp_gradient", "ys_mlp_train_step", "ys_mlp_features", "ys_mlp_correct",
@@ -269,6 +271,18 @@ class Plan:
         r = self._cat(*ran)
         self._keep = (gal, ran)
         _check(_lib().ys_assign(self._h, ctypes.byref(g), ctypes.byref(r)), "ys_assign")
+
+    def cache_randoms(self, ran):
+        """ys_randoms_cache: deposit these randoms once (device tensors x, y, z, w, nbar)."""
+        r = self._cat(*ran)
+        self._keep_ran = ran
+        _check(_lib().ys_randoms_cache(self._h, ctypes.byref(r)), "ys_randoms_cache")
+
+    def assign_cached(self, gal):
+        """ys_assign_cached: the galaxies against the kept randoms."""
+        g = self._cat(*gal)
+        self._keep = (gal, None)
+        _check(_lib().ys_assign_cached(self._h, ctypes.byref(g)), "ys_assign_cached")
 
     def measure_async(self, d_out=None):
         _check(_lib().ys_measure_multipoles_async(self._h, _ptr(d_out)), "ys_measure_multipoles_async")

@@ -383,10 +383,11 @@ def workload(name: str, scale: float = 1.0):
         gal, ran, geo = zeldovich_cone(int(1_000_000 * scale), int(5_000_000 * scale))
         return gal, ran, geo, dict(n_mesh=256, assign="tsc", interlace=True, ell_max=4,
                                    k_min=0.0, dk=0.01, k_max=None)
-    if name == "paper512_cic":
+    if name in ("paper512_cic", "paper1024_cic"):
+        # the same mock on the two meshes of the paper's timing table (Table 1)
         gal, ran, geo = paper_cap(int(525_000 * scale), int(5_250_000 * scale))
-        return gal, ran, geo, dict(n_mesh=512, assign="cic", interlace=False, ell_max=4,
-                                   k_min=0.0, dk=0.01, k_max=None)
+        return gal, ran, geo, dict(n_mesh=512 if name == "paper512_cic" else 1024, assign="cic",
+                                   interlace=False, ell_max=4, k_min=0.0, dk=0.01, k_max=None)
     if name == "shell512_tsc_il":
         gal, ran, geo = poisson_shell(int(10_000_000 * scale), int(50_000_000 * scale))
         return gal, ran, geo, dict(n_mesh=512, assign="tsc", interlace=True, ell_max=4,
