@@ -138,15 +138,25 @@ template <> struct Dft<8> {
   }
 };
 
-// Element offset inside a line: with PAD, one complex of padding follows every 8
-// elements, which spreads the strided Stockham stores over the shared-memory banks.
+// Element offset inside a line: with PAD, one complex of padding follows every 16
+// elements.  A float2 access is served per half-warp over 16 bank pairs, so 16
+// consecutive elements that start on a multiple of 16 stay on 16 distinct pairs,
+// while the strided Stockham stores (element R j + r, R = 8 or 4) are spread over the
+// pairs by the pad.
 template <bool PAD>
-__host__ __device__ constexpr int fft_pos(int i) { return PAD ? i + (i >> 3) : i; }
+__host__ __device__ constexpr int fft_pos(int i) { return PAD ? i + (i >> 4) : i; }
 
-// Line length in complex elements for a padded / unpadded layout (odd, so that
-// consecutive lines start in different banks).
-template <int N, bool PAD>
-__host__ __device__ constexpr int fft_line_len() { return PAD ? N + N / 8 + 1 : N + 1; }
+// Line length in complex elements for a padded / unpadded layout.  Padded lines are
+// 1 mod 16 (lines read at one element by 16 row lanes land on 16 pairs), or 2 mod 16
+// when ROWS_ARE_PAIRS (8 rows x 2 elements per half-warp, the split of the y,z
+// stage's row items from 512^3 up); unpadded ones are odd.
+template <int N, bool PAD, bool ROWS_ARE_PAIRS = false>
+__host__ __device__ constexpr int fft_line_len() {
+  if (!PAD) return N + 1;
+  const int base = N + N / 16;
+  const int want = ROWS_ARE_PAIRS ? 2 : 1;
+  return base + ((want - base % 16) + 16) % 16;
+}
 
 // Twiddles are stored stage by stage: for stage s >= 1 (N_s = fft_ns_before(N, s)
 // elements already combined, radix R_s), entry k (R_s - 1) + r - 1 of the stage's
@@ -166,10 +176,12 @@ __host__ __device__ constexpr int fft_tw_offset(int n, int stage) {
 // by a line-group barrier so that no pass's addresses are hoisted into another);
 // NL == 0: nl lines at run time.
 //
-// Padded lines walked by consecutive threads (the y,z stage) take a fast path when the
-// threads per line, the input stride and N_s are multiples of 8: element i sits at
-// i + i/8, and (a + 8 m)/8 = a/8 + m, so every load and store is one per-thread base
-// address plus a compile-time offset.
+// Padded lines walked by consecutive threads (the y,z stage) take a fast path: element
+// i sits at i + i/16, and (a + 16 m)/16 = a/16 + m, so when the threads per line and
+// the input stride are multiples of 16 every load is one per-thread base address plus
+// a compile-time offset.  The stores go to outb + r N_s with outb = k (mod N_s R): for
+// N_s a multiple of 16 the same holds, and for N_s dividing 16 (with k < N_s and N_s R
+// a multiple of 16) element outb + r N_s sits at pos(outb) + r N_s + (r N_s)/16.
 template <int N, int S, bool LF, bool PAD, int NL = 0>
 __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt, const float2* tw) {
   constexpr int R = fft_radix(N, S);
@@ -178,7 +190,8 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
   constexpr int NB = E / R;         // butterflies per thread
   constexpr int NS = fft_ns_before(N, S);
   constexpr int STRIDE = N / R;
-  constexpr bool FAST = !LF && PAD && TPL % 8 == 0 && STRIDE % 8 == 0 && NS % 8 == 0;
+  constexpr bool FAST_LD = !LF && PAD && TPL % 16 == 0 && STRIDE % 16 == 0;
+  constexpr bool FAST_ST = !LF && PAD && (NS % 16 == 0 || (16 % NS == 0 && (NS * R) % 16 == 0));
   const float2* tws = tw + fft_tw_offset(N, S);
   // Lines walked by consecutive threads only need their own threads synchronised.
   const int tid = threadIdx.x;
@@ -194,12 +207,12 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
     float2 v[E];
     if (ok) {
       const float2* lp = buf + line * ls;
-      if constexpr (FAST) {
-        const float2* src = lp + (tl + (tl >> 3));
+      if constexpr (FAST_LD) {
+        const float2* src = lp + (tl + (tl >> 4));
 #pragma unroll
         for (int q = 0; q < NB; ++q)
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = src[(q * TPL + r * STRIDE) / 8 * 9];
+          for (int r = 0; r < R; ++r) v[q * R + r] = src[(q * TPL + r * STRIDE) / 16 * 17];
       } else {
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
@@ -223,10 +236,10 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
         }
         Dft<R>::run(&v[q * R]);
         const int outb = (j / NS) * NS * R + k;
-        if constexpr (FAST) {
-          float2* dst = lp + (outb + (outb >> 3));
+        if constexpr (FAST_ST) {
+          float2* dst = lp + (outb + (outb >> 4));
 #pragma unroll
-          for (int r = 0; r < R; ++r) dst[r * NS / 8 * 9] = v[q * R + r];
+          for (int r = 0; r < R; ++r) dst[r * NS + (r * NS) / 16] = v[q * R + r];
         } else {
 #pragma unroll
           for (int r = 0; r < R; ++r) lp[fft_pos<PAD>(outb + r * NS) * es] = v[q * R + r];
@@ -364,8 +377,8 @@ __device__ __forceinline__ void fft_stage0_regs(float2 (&v)[fft_elems(N)], float
   for (int q = 0; q < E / R; ++q) {
     Dft<R>::run(&v[q * R]);
     const int j = tl + q * TPL;
-    if constexpr (PAD && R == 8) {
-      float2* dst = lp + 9 * j * es;  // element 8 j + r sits at 9 j + r
+    if constexpr (PAD && 16 % R == 0) {
+      float2* dst = lp + fft_pos<true>(j * R) * es;  // element R j + r sits r after R j (R | 16)
 #pragma unroll
       for (int r = 0; r < R; ++r) dst[r * es] = v[q * R + r];
     } else {

@@ -143,12 +143,15 @@ struct YZ {
   static constexpr int R0WS = (N >= 512 ? 8 : 16);
   static constexpr int R = (LPP > R0WS ? (LPP < N ? LPP : N) : R0WS);  // rows per row item
   static constexpr int PASSES = (R + LPP - 1) / LPP;
-  static constexpr int LL = fft_line_len<N, true>();         // padded line length
+  static constexpr int LL = fft_line_len<N, true, (R0WS == 8)>();  // padded line length
   static constexpr size_t smem_z = sizeof(float2) * 2 * R * LL;
   static constexpr size_t smem_y = sizeof(float2) * NB * LL;
   static constexpr size_t smem_nodes = sizeof(float2) * R * N;  // (F, 1/|r|^2) per node of a row item
   static constexpr size_t smem = sizeof(float2) * N + smem_nodes + (smem_z > smem_y ? smem_z : smem_y);
   static_assert(N % R == 0, "rows per item must divide N");
+  // Resident CTAs per SM the register budget is set for: two when two CTAs' shared
+  // memory fits the SM (228 KB, less 1 KB reserved per CTA), else one.
+  static constexpr int MIN_BLOCKS = 2 * (smem + 1024 + 64) <= 228 * 1024 ? 2 : 1;
 };
 
 
@@ -188,8 +191,8 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
         }
         Dft<R0>::run(v);
         const int jq = tl + q * TPL;
-        if constexpr (R0 == 8) {
-          float2* dst = lp + 9 * jq;  // element 8 jq + r sits at 9 jq + r
+        if constexpr (16 % R0 == 0) {
+          float2* dst = lp + fft_pos<true>(jq * R0);  // element R0 jq + r sits r after R0 jq
 #pragma unroll
           for (int r = 0; r < R0; ++r) dst[r] = v[r];
         } else {
@@ -202,10 +205,11 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
   line_group_sync<TPL>();  // each line is written and read by its own threads
   FftRun<N, 1, false, true, R>::run(C, 1, LL, R, tw);
   __syncthreads();
-  // Split: thread t takes row r = t mod R and k_z = t / R + i KS.  KS is a multiple
-  // of 8, so the padded positions of k_z and N - k_z move by fixed steps.
-  static_assert(Y::THREADS % R == 0 && (Y::THREADS / R) % 8 == 0, "split stride");
-  constexpr int KS = Y::THREADS / R, PSTEP = KS / 8 * 9;
+  // Split: thread t takes row r = t mod R and k_z = t / R + i KS.  When KS is a
+  // multiple of 16 the padded positions of k_z and N - k_z move by fixed steps.
+  static_assert(Y::THREADS % R == 0, "split stride");
+  constexpr int KS = Y::THREADS / R, PSTEP = KS / 16 * 17;
+  constexpr bool STEP = KS % 16 == 0;
   const int r = threadIdx.x % R, kz0 = threadIdx.x / R;
   const float2* crow = C + r * LL;
   const float2* pk = crow + fft_pos<true>(kz0);
@@ -213,8 +217,8 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
   float2* za = zslot + ((size_t)fa * nzc + kz0) * N + row0 + r;
   const size_t fstep = (size_t)nzc * N;
   for (int kz = kz0; kz < nzc; kz += KS, pk += PSTEP, pm -= PSTEP, za += (size_t)KS * N) {
-    const float2 ck = *pk;
-    const float2 cm = kz ? *pm : ck;
+    const float2 ck = STEP ? *pk : crow[fft_pos<true>(kz)];
+    const float2 cm = kz ? (STEP ? *pm : crow[fft_pos<true>(N - kz)]) : ck;
     // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i).
     za[0] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
     if (fb < NB) za[fstep] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
@@ -265,7 +269,11 @@ __device__ __forceinline__ void column_fold(const float2* S, int kz, const int* 
   const int kymax = (cnt - 1) / 2;
   const size_t gstep = (size_t)N * np;  // between groups
   float2* g0 = gout + ((size_t)j * NG * N + ix) * np + p0;
-  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+  // Lanes start at a multiple of 16 of the line position (k_y = -kymax sits at
+  // N - kymax), so each half-warp reads 16 consecutive, 16-aligned elements.
+  const int lead = (N - kymax) & 15;
+  for (int q = (int)threadIdx.x - lead; q < cnt; q += blockDim.x) {
+    if (q < 0) continue;
     const int ky = q - kymax;
     const float2* sp = S + fft_pos<true>(ky < 0 ? ky + N : ky);
     float2 g[NG];
@@ -318,13 +326,8 @@ __device__ __forceinline__ void signal_release(int* counter) {
   if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(counter) : "memory");
 }
 
-// Resident CTAs per SM the y,z kernel is compiled for (register budget 65536 / (256 x this)).
-#ifndef YS_YZ_MIN_BLOCKS
-#define YS_YZ_MIN_BLOCKS 2
-#endif
-
 template <int N, int ELL>
-__global__ void __launch_bounds__(256, (N >= 1024 ? 1 : YS_YZ_MIN_BLOCKS)) k_yz(YZParams prm) {
+__global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(YZParams prm) {
   using Y = YZ<N, ELL>;
   constexpr int R = Y::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];

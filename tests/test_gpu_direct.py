@@ -37,7 +37,12 @@ def _raw(ref):
     return has, np.where(has, ref.sum0 / np.where(has, ref.n_modes, 1) / ref.norm.I, 0.0)
 
 
-def check(res, ref, ells, label, tol=TOL):
+# P_6 of the FFT path: the bar derived in test_gpu_l6 (float32 transforms amplified
+# by the l = 6 combination); the direct sums themselves keep 1e-4.
+TOL_P6_FFT = 3e-4
+
+
+def check(res, ref, ells, label, tol=TOL, tol6=TOL):
     np.testing.assert_array_equal(res.n_modes, ref.n_modes)
     has, raw = _raw(ref)
     np.testing.assert_allclose(res.k[has], ref.k[has], rtol=1e-12)
@@ -48,7 +53,7 @@ def check(res, ref, ells, label, tol=TOL):
         assert sel.any(), (label, l)
         rel = np.abs(g[sel] - o[sel]) / np.abs(o[sel])
         worst[l] = float(rel.max())
-        assert rel.max() <= tol, (label, l, rel.max())
+        assert rel.max() <= (tol6 if l == 6 else tol), (label, l, rel.max())
     print(f"{label}: worst rel err per multipole {worst}")
 
 
@@ -111,7 +116,7 @@ def test_sum_gal_equals_fft_path_ngp_on_nodes():
         ff = plan.measure()
     ref = oracle.sum_gal(gal, ran, geo, n, bins, ell_max=6)
     check(sg, ref, (0, 2, 4, 6), "ngp_nodes_sum_gal")
-    check(ff, ref, (0, 2, 4, 6), "ngp_nodes_fft")
+    check(ff, ref, (0, 2, 4, 6), "ngp_nodes_fft", tol6=TOL_P6_FFT)
 
 
 @pytest.mark.parametrize("n,kind,interlace,compensate", [
