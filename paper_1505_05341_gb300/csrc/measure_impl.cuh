@@ -77,17 +77,41 @@ cudaError_t run_x(Plan& p) {
   int dev0 = 0, smem_max = 0;
   if ((err = cudaGetDevice(&dev0))) return err;
   if ((err = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0))) return err;
-  // one float-bin copy per warp while it fits, else one shared copy (many shells)
-  const int nwb = XC::smem(nbins, XC::NW) <= (size_t)smem_max ? XC::NW : 1;
+  // Float-bin copies: several per warp (lanes spread over them) while that costs no
+  // resident CTA, else one per warp while it fits, else one shared copy (many shells).
+  auto occupancy = [&](int nwb, int* per) -> cudaError_t {
+    const size_t sm = XC::smem(nbins, nwb);
+    if (sm > (size_t)smem_max) {
+      *per = 0;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_x_combine<N, ELL, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_x_combine<N, ELL, M>, XC::THREADS, sm);
+    return e;
+  };
+  int nwb = 1, per = 0, per_warp = 0;
+  if ((err = occupancy(XC::NW, &per_warp))) return err;
+  if (per_warp > 0) {
+    nwb = XC::NW;
+    per = per_warp;
+    for (int c : {4, 2}) {
+      int pc = 0;
+      if ((err = occupancy(XC::NW * c, &pc))) return err;
+      if (pc >= per_warp) {
+        nwb = XC::NW * c;
+        break;
+      }
+    }
+  } else if ((err = occupancy(1, &per))) {
+    return err;
+  }
   const size_t smem = XC::smem(nbins, nwb);
   if (smem > (size_t)smem_max) return cudaErrorInvalidConfiguration;
   if ((err = cudaFuncSetAttribute(k_x_combine<N, ELL, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return err;
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   if ((err = cudaGetDevice(&dev))) return err;
   if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
-  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_x_combine<N, ELL, M>, XC::THREADS, smem)))
-    return err;
   const int npb = p.np_pad / XC::P;
   const int grid = std::max(1, std::min(npb, std::max(1, per) * sms));
   LaunchScope ls(p, 6);

@@ -389,13 +389,21 @@ __host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >
 __host__ __device__ constexpr int group_first(int g) { return g == 0 ? 0 : (g <= 3 ? 1 : (g <= 8 ? 4 : 9)); }
 __host__ __device__ constexpr int group_last(int g) { return g == 0 ? 0 : (g <= 3 ? 3 : (g <= 8 ? 8 : 15)); }
 
-// Group transformed at tile position q of a pencil block.  For l_max = 6 the powers of
+// Group transformed at tile position q of a pencil block.  With HORNER the powers of
 // k_x of each multipole come highest first, so that the x stage can sum them by
 // Horner's rule (see k_x_combine); otherwise in table order.
-template <int ELL>
+template <bool HORNER>
 __host__ __device__ constexpr int tile_group(int q) {
-  return ELL == 6 ? group_first(q) + group_last(q) - q : q;
+  return HORNER ? group_first(q) + group_last(q) - q : q;
 }
+
+// Whether the x stage sums the k_x powers of each multipole by the compensated
+// Horner scheme (see k_x_combine): always for l_max = 6, and for l_max = 2, 4 except
+// at 256^3 and 512^3, where the x stage is held to 80 registers for three CTAs per SM
+// and the extra error terms would spill (shells there hold many modes, and the
+// plain sums meet the parity bar with a wide margin).
+template <int N, int ELL>
+__host__ __device__ constexpr bool x_horner() { return ELL == 6 || (ELL >= 2 && N != 256 && N != 512); }
 
 // ---------------------------------------------------------------------------
 // x stage: FFT along x of every (mesh, group) tile of P pencils, fed by TMA.
@@ -478,8 +486,11 @@ struct XCombine {
   // resident CTAs per SM the register budget is set for (3 x 256 threads from 256^3 up)
   static constexpr int MIN_BLOCKS = ((N == 256 || N == 512) && ELL <= 4) ? 3 : 1;
   static_assert(THREADS % 32 == 0, "threads");
-  // nwb copies of the compensated float shell bins (one per warp when they fit; warp
-  // w adds into copy w mod nwb): a sum and an error term per shell and slot
+  // nwb copies of the compensated float shell bins: a sum and an error term per shell
+  // and slot.  With nwb = NW c (c copies per warp) lane l of warp w adds into copy
+  // w c + l mod c, which divides the lanes that hit one address in one instruction
+  // (same-address shared atomics are served one after another); with fewer copies
+  // warp w adds into copy w mod nwb.
   static size_t smem(int nbins, int nwb) {
     size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
@@ -496,6 +507,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
             int* __restrict__ err) {
   using XC = XCombine<N, ELL, M>;
   constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, TILES = XC::TILES, RL = XC::RL;
+  constexpr bool HORNER = x_horner<N, ELL>();
   constexpr int NBL = E / RL;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bar[2];
@@ -528,7 +540,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   const int total = mine * TILES;
   auto issue = [&](int s) {
     const int k = s / TILES, t = s - k * TILES;
-    const int gi = tile_group<ELL>(t / M), mj = t - (t / M) * M;
+    const int gi = tile_group<HORNER>(t / M), mj = t - (t / M) * M;
     const int pb = blockIdx.x + k * gridDim.x;
     float2* dst = T0 + (s & 1) * N * P;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -540,7 +552,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
   if (tid == 0 && total > 0) issue(0);
   const int p = tid % P, tl = tid / P;
   float2 a0[E], ga[E];
-  float2 gl[ELL == 6 ? E : 1];  // l = 6: rounding errors of the Horner sums in ga
+  float2 gl[HORNER ? E : 1];  // rounding errors of the Horner sums in ga
   int bins[E];  // shell of each of this thread's modes in the current pencil (-1: none)
   int ky = 0, kz = -1, iyk = 0;
   float cf_pen = 0.f;
@@ -555,7 +567,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
       break;
     }
     const int k = s / TILES, t = s - k * TILES;
-    const int gi = tile_group<ELL>(t / M), mj = t - (t / M) * M;
+    const int gi = tile_group<HORNER>(t / M), mj = t - (t / M) * M;
     if (t == 0) {
       const short2 pc = pencil[(blockIdx.x + k * gridDim.x) * P + p];
       ky = pc.x;
@@ -591,7 +603,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
         const int mx = kx <= N / 2 ? kx : kx - N;
         float2 X = v[e];
         if (M == 2 && mj == 1) X = cmul(X, cmul(phs[kx], ph_pen));
-        if (ELL == 6 && gi != 0) {
+        if (HORNER && gi != 0) {
           // sum_p m_x^p X_p by Horner's rule (highest power first), every step
           // error-free: the product by the integer m_x is split exactly with an FMA
           // and the add with TwoSum, and both errors go to gl.  The window and the
@@ -623,10 +635,10 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
         }
       }
     // a multipole is complete after its last tile (for l = 6 its power-0 group)
-    const bool complete = (mj == M - 1) && (ELL == 6 ? gi == group_first(gi) : gi == group_last(gi));
+    const bool complete = (mj == M - 1) && (HORNER ? gi == group_first(gi) : gi == group_last(gi));
     if (complete) {
       const int slot = gi == 0 ? 0 : (gi <= 3 ? 1 : (gi <= 8 ? 2 : 3));
-      if (ELL == 6 && slot > 0) {
+      if (HORNER && slot > 0) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int kx = tl + (e / RL) * TPL + (e % RL) * (N / RL);
@@ -634,7 +646,8 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
           ga[e] = make_float2(c * (ga[e].x + gl[e].x), c * (ga[e].y + gl[e].y));
         }
       }
-      float* wb = wbin + ((warp % nwb) * SLOTS + slot) * nbins;
+      const int copy = nwb >= XC::NW ? warp * (nwb / XC::NW) + (tid & 31) % (nwb / XC::NW) : warp % nwb;
+      float* wb = wbin + (copy * SLOTS + slot) * nbins;
       float* wc = wb + nwb * SLOTS * nbins;
       const float wgt = kz == 0 ? 1.f : 2.f;
       // Half of the modes at a time: their sums first, so that the atomics' latencies
