@@ -347,8 +347,12 @@ def run_ours(args):
         plan.measure_async(out)
 
     # launch shapes for this configuration (scatter tile, y,z grid and ring lead),
-    # chosen once before any timing
-    tuning = plan.autotune(dgal, dran, reps=2)
+    # chosen once before any timing (--no-tune keeps the defaults, so that a
+    # profiler sees a fixed launch sequence)
+    if args.no_tune:
+        tuning = None
+    else:
+        tuning = plan.autotune(dgal, dran, reps=2)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -439,7 +443,8 @@ def run_ours(args):
                    "n_gal": gal.n, "n_ran": ran.n, "k_max": K_MAX, "dk": DK, "fields": "1+6+15",
                    "l2": "inputs larger than L2 (0.96 GB catalogue, 1 GB meshes, 11 GB spectra)",
                    "parallelism": f"replicas{world}", "seeds": seeds_record(rank, args.workload),
-                   "tuned": {"tile": list(tuning.tile), "yz_grid": tuning.yz_grid, "ring_lead": tuning.ring_lead}},
+                   "tuned": ({"tile": list(tuning.tile), "yz_grid": tuning.yz_grid, "ring_lead": tuning.ring_lead}
+                             if tuning is not None else "defaults (--no-tune)")},
         "roofline": roofline,
         "step_roofline": {"bound": "hbm", "alg_bytes": b_alg, "achieved_GBps": b_alg / (ms_step / 1e3) / 1e9,
                           "peak_GBps": peak, "frac": b_alg / (ms_step / 1e3) / 1e9 / peak, "peak_source": peak_src},
@@ -830,6 +835,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (fixed launch sequence for profiling)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -286,9 +286,10 @@ ys_status ys_plan_destroy(ys_plan* plan);
 /* ---- Autotuning and batched runs (throughput arrangements; no counterpart in the
  * paper's equations, which these calls evaluate unchanged) ---- */
 
-/* Launch shapes the autotuner chose: scatter tile (nodes per axis), CTAs of the
- * persistent y,z kernel and the lead (in x-planes) of its column items over its row
- * items, with the best measured times. */
+/* Launch shapes the autotuner chose: scatter tile (nodes per axis; 0 0 0 = the direct
+ * assignment, see ys_plan_set_direct_assign), CTAs of the persistent y,z kernel and
+ * the lead (in x-planes) of its column items over its row items, with the best
+ * measured times. */
 typedef struct {
   int32_t tile[3];
   int32_t yz_grid;
@@ -297,13 +298,21 @@ typedef struct {
   double measure_ms;
 } ys_tuning;
 
-/* Time the candidate scatter tiles (16x16x32, 8x16x32, 16x16x16, 32x16x32, 8x8x32),
- * y,z grids (resident, 3/4, 1/2) and ring leads (0.7x, 1x, 1.4x, 2x a work-balanced
- * estimate) on this catalogue (DEVICE pointers), reps timed calls each, and keep the
- * fastest in the plan.  Leaves the catalogue assigned.
- * Synchronous.  out may be NULL. */
+/* Time the candidate scatter tiles (16x16x32, 8x16x32, 16x16x16, 32x16x32, 8x8x32)
+ * and, for small meshes, the direct assignment; then the y,z grids (resident, 3/4,
+ * 1/2) and ring leads (0.7x, 1x, 1.4x, 2x a work-balanced estimate) on this catalogue
+ * (DEVICE pointers), reps timed calls each, and keep the fastest in the plan.  Leaves
+ * the catalogue assigned.  Synchronous.  out may be NULL. */
 ys_status ys_plan_autotune(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran, int32_t reps,
                            ys_tuning* out);
+
+/* Choose the assignment's arrangement (Eq. 1 either way): enable != 0 selects the
+ * direct assignment, which reads each catalogue twice (its weights for alpha, I and
+ * S, then its particles) and adds every stencil weight into the zeroed mesh with
+ * global float reductions that stay in L2 -- offered when the plan's meshes hold at
+ * most 64 MB (YS_ERR_UNSUPPORTED above); 0 selects the tile-sorted assignment (the
+ * default).  ys_plan_autotune sets it by timing both.  Host-side. */
+ys_status ys_plan_set_direct_assign(ys_plan* plan, int enable);
 
 typedef struct ys_batch_s ys_batch;
 

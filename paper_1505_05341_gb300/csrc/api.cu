@@ -496,6 +496,8 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
     p.ntiles_max = std::max(p.ntiles_max, p.ntiles);
   }
   ys::set_tiles(p, ys::TILE_X, ys::TILE_Y, ys::TILE_Z);
+  // a mesh set of at most 64 MB (half of L2) can stay in L2 during the direct assignment
+  p.direct_ok = (size_t)p.m * n * n * n * sizeof(float) <= (64u << 20);
   ys_status st = ys::build_tables(p);
   if (st != YS_OK) {
     ys::free_all(p);
@@ -777,6 +779,14 @@ ys_status ys_plan_set_fault_injection(ys_plan* plan, int64_t wait_limit_ns, int3
     cudaGraphExecDestroy(p.measure_exec);
     p.measure_exec = nullptr;
   }
+  return YS_OK;
+}
+
+ys_status ys_plan_set_direct_assign(ys_plan* plan, int enable) {
+  if (!plan) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  if (enable && !p.direct_ok) return YS_ERR_UNSUPPORTED;
+  p.direct_assign = enable != 0;
   return YS_OK;
 }
 

@@ -352,6 +352,128 @@ __global__ void k_ran_sums(const float* __restrict__ w, const float* __restrict_
 
 // rmesh != nullptr (shared randoms): ran is empty, the random sums come from rsums
 // (sum w, sum w^2, sum w^2 nbar) and the deposit subtracts alpha rmesh.
+// ---------------------------------------------------------------------------
+// Direct assignment for meshes that stay resident in L2 (m N^3 floats of at most
+// 64 MB, half of it): one pass over each catalogue adds every stencil weight
+// into the zeroed mesh with global float reductions, served in L2.  The catalogue
+// sums come first (the randoms carry -alpha w), so particles are read twice in all
+// (4-12 bytes, then 16) instead of the sort's count, bin and deposit passes.
+// ---------------------------------------------------------------------------
+
+// Catalogue sums of Eqs. (1) and (3): Kahan-compensated float per thread, FP64
+// across threads (the same slots as the sorted path's counting pass).
+__global__ void __launch_bounds__(THREADS)
+k_sums(const float* __restrict__ pw, const float* __restrict__ pnbar, int64_t n, int is_ran,
+       double* __restrict__ sums) {
+  float s_w = 0.f, c_w = 0.f, s_w2 = 0.f, c_w2 = 0.f, s_w2n = 0.f, c_w2n = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+    const float w = pw ? pw[idx] : 1.f;
+    float yv = w - c_w, t = s_w + yv;
+    c_w = (t - s_w) - yv; s_w = t;
+    yv = w * w - c_w2; t = s_w2 + yv;
+    c_w2 = (t - s_w2) - yv; s_w2 = t;
+    if (is_ran && pnbar) {
+      yv = w * w * pnbar[idx] - c_w2n; t = s_w2n + yv;
+      c_w2n = (t - s_w2n) - yv; s_w2n = t;
+    }
+  }
+  const double v0 = warp_sum((double)s_w - (double)c_w);
+  const double v1 = warp_sum((double)s_w2 - (double)c_w2);
+  const double v2 = warp_sum((double)s_w2n - (double)c_w2n);
+  if ((threadIdx.x & 31) == 0) {
+    if (is_ran) {
+      atomicAdd(&sums[SUM_WR], v0);
+      atomicAdd(&sums[SUM_WR2], v1);
+      atomicAdd(&sums[SUM_WR2N], v2);
+    } else {
+      atomicAdd(&sums[SUM_WG], v0);
+      atomicAdd(&sums[SUM_WG2], v1);
+    }
+  }
+}
+
+template <int KIND, int M>
+__global__ void __launch_bounds__(THREADS)
+k_direct(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
+         const float* __restrict__ pw, int64_t n, int is_ran, Geom g, const float2* __restrict__ nodes,
+         double* __restrict__ sums, double alpha_cfg, float* __restrict__ mesh) {
+  float wscale = 1.f;
+  if (is_ran) wscale = (float)(-(alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR]));
+  const int nn = g.n;
+  const size_t n3 = (size_t)nn * nn * nn;
+  unsigned bad = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+    const float x = px[idx], y = py[idx], z = pz[idx];
+    const float w = (pw ? pw[idx] : 1.f) * wscale;
+    int ci[3];
+    float cd[3];
+    bool ok = locate(x, 0, g, nodes, ci[0], cd[0]);
+    ok &= locate(y, 1, g, nodes, ci[1], cd[1]);
+    ok &= locate(z, 2, g, nodes, ci[2], cd[2]);
+    bad += ok ? 0u : 1u;
+#pragma unroll
+    for (int mj = 0; mj < M; ++mj) {
+      int node[3][3];
+      float wt[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int first;
+        stencil<KIND>(ci[a], cd[a], mj == 1, first, wt[a]);
+#pragma unroll
+        for (int s = 0; s < KIND; ++s) node[a][s] = wrapn(first + s, nn);
+      }
+      float* mm = mesh + mj * n3;
+#pragma unroll
+      for (int a = 0; a < KIND; ++a)
+#pragma unroll
+        for (int b = 0; b < KIND; ++b) {
+          const float wxy = w * wt[0][a] * wt[1][b];
+          float* row = mm + ((size_t)node[0][a] * nn + node[1][b]) * nn;
+#pragma unroll
+          for (int c = 0; c < KIND; ++c) atomicAdd(row + node[2][c], wxy * wt[2][c]);
+        }
+    }
+  }
+  unsigned tot = bad;  // particles outside the box
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&sums[SUM_BAD], (double)tot);
+}
+
+template <int KIND, int M>
+cudaError_t run_direct(Plan& p, const ys_catalog& gal, const ys_catalog& ran) {
+  cudaStream_t st = p.stream;
+  cudaError_t err;
+  const size_t n3 = (size_t)p.n * p.n * p.n;
+  if ((err = cudaMemsetAsync(p.d_sums, 0, sizeof(double) * SUM_COUNT, st))) return err;
+  if ((err = cudaMemsetAsync(p.d_mesh, 0, sizeof(float) * p.m * n3, st))) return err;
+  int dev = 0, sms = 0;
+  if ((err = cudaGetDevice(&dev)) || (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+    return err;
+  auto blocks = [&](int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + THREADS - 1) / THREADS, (int64_t)sms * 8));
+  };
+  const ys_catalog* cats[2] = {&gal, &ran};
+  for (int c = 0; c < 2; ++c) {
+    const ys_catalog& k = *cats[c];
+    if (k.n == 0) continue;
+    LaunchScope ls(p, 0);
+    k_sums<<<blocks(k.n), THREADS, 0, st>>>(k.w, k.nbar, k.n, c, p.d_sums);
+    if ((err = cudaGetLastError())) return err;
+  }
+  for (int c = 0; c < 2; ++c) {
+    const ys_catalog& k = *cats[c];
+    if (k.n == 0) continue;
+    LaunchScope ls(p, 3);
+    k_direct<KIND, M><<<blocks(k.n), THREADS, 0, st>>>(k.x, k.y, k.z, k.w, k.n, c, p.geom, p.d_nodes, p.d_sums,
+                                                       p.cfg.alpha, p.d_mesh);
+    if ((err = cudaGetLastError())) return err;
+  }
+  return cudaSuccess;
+}
+
 template <int KIND, int M>
 cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, const float* rmesh = nullptr,
                        const double* rsums = nullptr) {
@@ -426,6 +548,17 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, co
 cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, const float* rmesh,
                           const double* rsums) {
   const int key = p.kind * 2 + (p.m - 1);
+  if (p.direct_assign && !rmesh) {
+    switch (key) {
+      case 2: return run_direct<1, 1>(p, gal, ran);
+      case 3: return run_direct<1, 2>(p, gal, ran);
+      case 4: return run_direct<2, 1>(p, gal, ran);
+      case 5: return run_direct<2, 2>(p, gal, ran);
+      case 6: return run_direct<3, 1>(p, gal, ran);
+      case 7: return run_direct<3, 2>(p, gal, ran);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (key) {
     case 2: return run_assign<1, 1>(p, gal, ran, rmesh, rsums);
     case 3: return run_assign<1, 2>(p, gal, ran, rmesh, rsums);

@@ -64,6 +64,19 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
   }
   const auto& bt = kTileCandidates[best_tile < 0 ? 0 : best_tile];
   set_tiles(p, bt[0], bt[1], bt[2]);
+  // 1b. direct assignment into an L2-resident mesh, where the mesh set is small enough
+  p.direct_assign = false;
+  if (p.direct_ok) {
+    p.direct_assign = true;
+    float ms = 0.f;
+    cudaError_t e1 = time_ms(p, reps, [&] { return launch_assign(p, gal, ran); }, &ms);
+    if (e1) {
+      why = cudaGetErrorString(e1);
+      return YS_ERR_CUDA;
+    }
+    if (ms < best_assign) best_assign = ms;
+    else p.direct_assign = false;
+  }
   cudaError_t e = launch_assign(p, gal, ran);
   if (e) {
     why = cudaGetErrorString(e);
@@ -115,7 +128,7 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
     p.ms[c] = 0.0;
   }
   if (out) {
-    for (int a = 0; a < 3; ++a) out->tile[a] = p.geom.tdim[a];
+    for (int a = 0; a < 3; ++a) out->tile[a] = p.direct_assign ? 0 : p.geom.tdim[a];
     out->yz_grid = p.yz_grid;
     out->ring_lead = p.ring_lead;
     out->assign_ms = best_assign;

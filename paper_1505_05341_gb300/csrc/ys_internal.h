@@ -58,6 +58,8 @@ struct Plan {
   long long yz_wait_ns = 1000000000LL;  // bound of each y,z-stage wait (ns)
   int fault_skip_plane = -1;     // test hook: plane whose row items withhold their completion
   int ntiles_max = 0;            // tile-counter capacity over the scatter tile candidates
+  bool direct_assign = false;    // assignment by global reductions into an L2-resident mesh
+  bool direct_ok = false;        // the mesh set is small enough for it (m N^3 floats <= 64 MB)
   // device tables
   float2* d_tw = nullptr;        // [n] exp(-2 pi i j / n)
   float2* d_nodes = nullptr;     // [3][n + 3] node positions (hi, lo), index offset 1

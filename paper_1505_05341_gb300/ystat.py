@@ -115,6 +115,7 @@ def _lib():
         lib.ys_assign_cached.argtypes = [P, ctypes.POINTER(YsCatalog)]
         lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
         lib.ys_plan_set_fault_injection.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+        lib.ys_plan_set_direct_assign.argtypes = [P, ctypes.c_int]
         lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
         lib.ys_plan_autotune.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), ctypes.c_int32,
                                          ctypes.POINTER(YsTuning)]
@@ -146,6 +147,7 @@ def _lib():
                      "ys_measure_multipoles", "ys_estimate_host", "ys_plan_destroy",
                      "ys_plan_set_profiling", "ys_plan_get_stats", "ys_assign_noalloc", "ys_plan_autotune",
                      "ys_plan_set_fault_injection", "ys_randoms_cache", "ys_assign_cached",
+                     "ys_plan_set_direct_assign",
                      "ys_batch_create", "ys_batch_autotune", "ys_batch_run", "ys_batch_destroy",
                      "ys_mlp_create", "ys_mlp_get_state", "ys_mlp_set_state", "ys_mlp_forward",
                      "ys_mlp_gradient", "ys_mlp_train_step", "ys_mlp_features", "ys_mlp_correct",
@@ -341,6 +343,11 @@ class Plan:
         completion is withheld (-1: none)."""
         _check(_lib().ys_plan_set_fault_injection(self._h, int(wait_limit_ns), int(skip_plane)),
                "ys_plan_set_fault_injection")
+
+    def set_direct_assign(self, enable: bool):
+        """ys_plan_set_direct_assign: reductions into an L2-resident mesh (True) or the
+        tile-sorted assignment (False)."""
+        _check(_lib().ys_plan_set_direct_assign(self._h, int(bool(enable))), "ys_plan_set_direct_assign")
 
     def set_profiling(self, enable: bool):
         _check(_lib().ys_plan_set_profiling(self._h, int(bool(enable))), "ys_plan_set_profiling")

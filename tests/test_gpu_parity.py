@@ -216,3 +216,45 @@ def test_shell_limit_at_the_largest_mesh():
     with pytest.raises(ys.YstatError) as ei:
         ys.Plan(1024, (0.0, 0.0, 0.0), 1000.0, assign="cic", dk=1e-4, n_bins=4097)
     assert ei.value.status == ys.ystat.YS_ERR_ARG
+
+
+@pytest.mark.parametrize("n,kind,interlace", [(64, "tsc", True), (128, "cic", False), (96, "ngp", True)])
+def test_direct_assignment_matches_oracle_and_sorted(n, kind, interlace):
+    """The direct assignment (global reductions into an L2-resident mesh) against the
+    oracle, and against the tile-sorted assignment (two float evaluations: twice the
+    bar); particles outside the box are still reported."""
+    gal, ran, geo = synth.zeldovich_cube(60_000, 300_000, seed=77)
+    bins = BinSpec.up_to(np.pi * n / geo.box_len, 0.01)
+    ref = oracle.fft_multipoles(gal, ran, geo, n, bins, assign=kind, interlace=interlace)
+    with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign=kind, interlace=interlace, dk=bins.dk,
+                 n_bins=bins.n_bins, stream=torch.cuda.current_stream().cuda_stream) as plan:
+        dg, dr = to_dev(gal), to_dev(ran)
+        plan.assign(dg, dr)
+        sorted_res = plan.measure()
+        plan.set_direct_assign(True)
+        plan.assign(dg, dr)
+        direct_res = plan.measure()
+    compare(direct_res, ref, 4, f"direct_{n}_{kind}_{interlace}")
+    has = ref.n_modes > 0
+    raw = np.where(has, ref.sum0 / np.where(has, ref.n_modes, 1) / ref.norm.I, 0.0)
+    for l in (0, 2, 4):
+        a, b = getattr(sorted_res, f"p{l}"), getattr(direct_res, f"p{l}")
+        sel = has & (np.abs(a) > 1e-2 * raw)
+        assert np.max(np.abs(a[sel] - b[sel]) / np.abs(a[sel])) <= 2 * TOL
+    out = synth.poisson_cube(100, 500, seed=2)
+    g2, r2, geo2 = out
+    g2.x[0] = geo2.box_min[0] - 5.0
+    with ys.Plan(32, geo2.box_min, geo2.box_len, geo2.observer, dk=0.05, n_bins=4,
+                 stream=torch.cuda.current_stream().cuda_stream) as plan:
+        plan.set_direct_assign(True)
+        plan.assign(to_dev(g2), to_dev(r2))
+        with pytest.raises(ys.YstatError) as ei:
+            plan.measure()
+        assert ei.value.status == ys.ystat.YS_ERR_ARG
+
+
+def test_direct_assignment_refused_for_large_meshes():
+    with ys.Plan(512, (0.0, 0.0, 0.0), 1000.0, dk=0.1, n_bins=4) as plan:
+        with pytest.raises(ys.YstatError) as ei:
+            plan.set_direct_assign(True)
+        assert ei.value.status == ys.ystat.YS_ERR_UNSUPPORTED
