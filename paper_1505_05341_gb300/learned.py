@@ -1,15 +1,25 @@
 """Learned aliasing/window correction: training pairs, GPU training, evaluation.
 
-The pairs come from the estimator itself: each seeded config-1-style mock (clustered
+The pairs come from the estimator itself.  Each seeded config-1-style mock (clustered
 Zel'dovich + RSD galaxies in a 500 Mpc/h cube centred on (600, 600, 600), observer at
-the origin, N_g uniform in 2e5-2e6, randoms 5 N_g) is measured on a coarse 128^3 CIC
-mesh without interlacing and on a fine 512^3 TSC mesh with interlacing, in shells of
-0.01 h/Mpc up to 0.80 h/Mpc (below the coarse Nyquist frequency, so both meshes see
-the same modes in every shell).  The network (ys_mlp, include/ystat.h) learns the
-scaled residual of each shell; training, inference and the correction all run in
-the library's kernels -- this module only sequences the calls.
+the origin, randoms 5 N_g) is measured on a coarse 128^3 CIC mesh without
+interlacing, in shells of 0.01 h/Mpc up to 0.80 h/Mpc (below the coarse Nyquist
+frequency).  Its target is one of:
+  * the fine 512^3 TSC mesh with interlacing (N_g uniform in 2e5-2e6), whose shells
+    see the same modes;
+  * on small cases (N_g uniform in 2e4-6e4), the direct galaxy sum of Sec. 4
+    (ys_sum_gal) at the coarse lattice's own modes: no mesh, window or aliasing.
+The network (ys_mlp, include/ystat.h) learns the scaled residual of each shell,
+trained on targets divided by their common RMS (the scale is folded back into the
+output layer afterwards, so the saved network predicts the residual itself).  The
+three outputs share that one scale: weighting P_2's residual, an order of magnitude
+smaller than the others, up to unit RMS made the network fit that residual's
+realisation-to-realisation noise, and the held-out P_2 residual grew (rms 6.1e-3 ->
+7.0e-3 on a short direct-sum training) instead of falling.
+Training, inference and the correction all run in the library's kernels -- this
+module only sequences the calls.
 
-    python -m paper_1505_05341_gb300.learned --train 2000 --heldout 200 --out weights.npz
+    python -m paper_1505_05341_gb300.learned --train 2000 --direct 200 --heldout 200 --out weights.npz
 """
 from __future__ import annotations
 
@@ -33,6 +43,11 @@ FINE = dict(n_mesh=512, assign="tsc", interlace=True)
 K_NYQ = math.pi * COARSE["n_mesh"] / BOX_LEN
 TRAIN_SEEDS = 10_000
 HELDOUT_SEEDS = 20_000
+DIRECT_SEEDS = 30_000          # small mocks with direct-sum targets (training)
+DIRECT_HELDOUT_SEEDS = 40_000  # and held out
+DIRECT_N_GAL = (20_000, 60_000)
+# parameter layout: W1 b1 W2 b2 W3 b3 W4[3][64] b4[3]; the output layer starts here
+W4_OFFSET = 5 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "correction_128cic_512tsc.npz")
 
 
@@ -80,6 +95,27 @@ class PairMaker:
         torch.cuda.synchronize()
         return out_c, out_f
 
+    def direct_rows(self, seeds):
+        """Device rows (len(seeds), stride) of the coarse mesh and of the direct galaxy
+        sum at the coarse lattice's modes, for small mocks (N_g in DIRECT_N_GAL)."""
+        import torch
+        import synth.gpu as sg
+        n = len(seeds)
+        out_c = torch.zeros((n, self.stride), dtype=torch.float64, device="cuda")
+        out_d = torch.zeros((n, self.stride), dtype=torch.float64, device="cuda")
+        for i, seed in enumerate(seeds):
+            ng, nr = sg.mock_sizes(seed, DIRECT_N_GAL)
+            gal, ran, _ = sg.zeldovich_cube(ng, nr, seed)
+            self.coarse.assign(gal, ran)
+            self.coarse.measure_async(out_c[i])
+            d = ystat.sum_gal(COARSE["n_mesh"], BOX_MIN, BOX_LEN, gal, ran, observer=OBSERVER, dk=DK,
+                              n_bins=N_BINS)
+            out_d[i] = torch.from_numpy(np.concatenate([d.k, d.n_modes, d.p0, d.p2, d.p4,
+                                                        [d.alpha, d.norm_I, d.shot_noise, 0.0, 0.0]]))
+            del gal, ran
+        torch.cuda.synchronize()
+        return out_c, out_d
+
     def close(self):
         self.coarse.close()
         self.fine.close()
@@ -113,6 +149,23 @@ def train(mlp, X, T, steps, lr=1e-3, lr_final=None, log_every=0):
             hist.append((s, float(sse.item()) / (3 * rows)))
     torch.cuda.synchronize()
     return hist
+
+
+def target_scales(T):
+    """The targets' common RMS, as a scale for each of the three outputs."""
+    import torch
+    return torch.sqrt(torch.mean(T.double() ** 2)).clamp_min(1e-12).float().repeat(3)
+
+
+def fold_scales(mlp, scales):
+    """A network trained on targets / scales predicts the residual itself once its
+    output layer (W4 row l and b4[l]) is multiplied by scales[l]."""
+    w, m, v, t = mlp.state()
+    sc = scales.cpu().numpy().astype(np.float32)
+    for l in range(3):
+        w[W4_OFFSET + 64 * l:W4_OFFSET + 64 * (l + 1)] *= sc[l]
+        w[W4_OFFSET + 3 * 64 + l] *= sc[l]
+    mlp.set_state(w, m, v, t)
 
 
 def residual_stats(rows, fine_rows):
@@ -158,6 +211,8 @@ def load(path=WEIGHTS):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--direct", type=int, default=200, help="small mocks with direct-sum targets")
+    ap.add_argument("--direct-heldout", type=int, default=20)
     ap.add_argument("--heldout", type=int, default=200)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -170,23 +225,49 @@ def main(argv=None):
     pm = PairMaker()
     tr_c, tr_f = pm.rows(list(range(TRAIN_SEEDS, TRAIN_SEEDS + a.train)))
     ho_c, ho_f = pm.rows(list(range(HELDOUT_SEEDS, HELDOUT_SEEDS + a.heldout)))
-    pm.close()
     t_pairs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dr_c = dr_d = dh_c = dh_d = None
+    if a.direct > 0:
+        dr_c, dr_d = pm.direct_rows(list(range(DIRECT_SEEDS, DIRECT_SEEDS + a.direct)))
+    if a.direct_heldout > 0:
+        dh_c, dh_d = pm.direct_rows(list(range(DIRECT_HELDOUT_SEEDS, DIRECT_HELDOUT_SEEDS + a.direct_heldout)))
+    pm.close()
+    t_direct = time.perf_counter() - t0
     X, T, _, m = features(tr_c, tr_f)
+    m_direct = 0
+    if dr_c is not None:
+        Xd, Td, _, m_direct = features(dr_c, dr_d)
+        X, T = torch.cat([X, Xd]), torch.cat([T, Td])
+    scales = target_scales(T)
     mlp = ystat.Mlp(init_params(a.seed))
     t1 = time.perf_counter()
-    hist = train(mlp, X, T, a.steps, a.lr, a.lr_final, log_every=max(1, a.steps // 20))
+    hist = train(mlp, X, (T / scales).contiguous(), a.steps, a.lr, a.lr_final, log_every=max(1, a.steps // 20))
+    fold_scales(mlp, scales)
+    torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     before, after = evaluate(mlp, ho_c, ho_f)
     tr_before, tr_after = evaluate(mlp, tr_c, tr_f)
+    d_before = d_after = None
+    if dh_c is not None:
+        d_before, d_after = evaluate(mlp, dh_c, dh_d)
     meta = dict(train_seeds=[TRAIN_SEEDS, TRAIN_SEEDS + a.train - 1],
-                heldout_seeds=[HELDOUT_SEEDS, HELDOUT_SEEDS + a.heldout - 1], rows=m, steps=a.steps,
+                heldout_seeds=[HELDOUT_SEEDS, HELDOUT_SEEDS + a.heldout - 1],
+                direct_seeds=[DIRECT_SEEDS, DIRECT_SEEDS + a.direct - 1] if a.direct else None,
+                direct_heldout_seeds=([DIRECT_HELDOUT_SEEDS, DIRECT_HELDOUT_SEEDS + a.direct_heldout - 1]
+                                      if a.direct_heldout else None),
+                direct_n_gal=list(DIRECT_N_GAL), rows=m, direct_rows=m_direct, steps=a.steps,
                 lr=a.lr, lr_final=a.lr_final, init_seed=a.seed, loss=hist, pair_seconds=t_pairs,
-                train_seconds=t_train, heldout_before=before, heldout_after=after, train_before=tr_before,
-                train_after=tr_after, coarse=COARSE, fine=FINE, dk=DK, n_bins=N_BINS)
+                direct_seconds=t_direct, train_seconds=t_train, target_scales=scales.cpu().tolist(),
+                heldout_before=before, heldout_after=after, train_before=tr_before, train_after=tr_after,
+                direct_heldout_before=d_before, direct_heldout_after=d_after, coarse=COARSE, fine=FINE, dk=DK,
+                n_bins=N_BINS,
+                note="Adam moments are those of the scaled-target training; the saved parameters "
+                     "have the scales folded into the output layer")
     save(a.out, mlp, meta)
-    print(json.dumps({k: meta[k] for k in ("rows", "pair_seconds", "train_seconds", "heldout_before",
-                                           "heldout_after", "train_before", "train_after")}))
+    print(json.dumps({k: meta[k] for k in ("rows", "direct_rows", "pair_seconds", "direct_seconds",
+                                           "train_seconds", "target_scales", "heldout_before",
+                                           "heldout_after", "direct_heldout_before", "direct_heldout_after")}))
     print("loss", hist[0], hist[-1])
     mlp.close()
     del torch

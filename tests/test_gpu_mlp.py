@@ -211,3 +211,52 @@ def test_training_lowers_heldout_residual(ys):
     print("held-out residual before", before, "after", after)
     assert after["rms0"] < 0.5 * before["rms0"]
     net.close()
+
+
+def test_folded_scales_reproduce_scaled_outputs(ys):
+    """A network trained on targets / s predicts the residual once s is folded into its
+    output layer: the folded outputs equal the unfolded ones times s."""
+    from paper_1505_05341_gb300 import learned
+    p = ref.init_params(21)
+    X, _ = _inputs(300, 21)
+    dX = torch.from_numpy(X).cuda()
+    net = ys.Mlp(p)
+    y0 = torch.empty((300, 3), dtype=torch.float32, device="cuda")
+    net.forward(dX, y0)
+    s = torch.tensor([0.08, 0.0065, 0.075], dtype=torch.float32)
+    learned.fold_scales(net, s)
+    y1 = torch.empty_like(y0)
+    net.forward(dX, y1)
+    torch.cuda.synchronize()
+    want = y0.cpu().numpy() * s.numpy()
+    got = y1.cpu().numpy()
+    # the kernels use bfloat16 weights: folding re-rounds the output layer
+    assert np.abs(got - want).max() <= 1e-2 * np.abs(want).max()
+    net.close()
+
+
+def test_direct_sum_targets_train_the_correction(ys):
+    """Pairs with the direct galaxy sum (Sec. 4) as target, on small mocks: a short
+    training on 12 of them must cut the held-out residual of the coarse monopole and
+    hexadecapole against the direct sum."""
+    from paper_1505_05341_gb300 import learned
+    pm = learned.PairMaker(max_particles=400_000)
+    old = learned.DIRECT_N_GAL
+    learned.DIRECT_N_GAL = (20_000, 30_000)
+    try:
+        tr_c, tr_d = pm.direct_rows(list(range(70_000, 70_012)))
+        ho_c, ho_d = pm.direct_rows(list(range(71_000, 71_004)))
+    finally:
+        learned.DIRECT_N_GAL = old
+    pm.close()
+    X, T, _, m = learned.features(tr_c, tr_d)
+    assert m > 10 * learned.N_BINS
+    scales = learned.target_scales(T)
+    net = ys.Mlp(learned.init_params(0))
+    learned.train(net, X, (T / scales).contiguous(), 800, lr=1e-3, lr_final=1e-4)
+    learned.fold_scales(net, scales)
+    before, after = learned.evaluate(net, ho_c, ho_d)
+    print("direct-sum targets: held-out residual before", before, "after", after)
+    assert after["rms0"] < 0.7 * before["rms0"]
+    assert after["rms4"] < 0.7 * before["rms4"]
+    net.close()

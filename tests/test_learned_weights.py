@@ -19,10 +19,15 @@ def test_weights_file():
     meta = json.loads(str(z["meta"]))
     assert meta["train_seeds"] == [10000, 11999] and meta["heldout_seeds"] == [20000, 20199]
     assert int(z["step"]) == meta["steps"]
-    # held-out monopole and hexadecapole residuals fell; the quadrupole did not grow much
+    # held-out residuals against the 512^3 targets: every multipole's RMS fell
     b, a = meta["heldout_before"], meta["heldout_after"]
     assert a["rms0"] < 0.1 * b["rms0"] and a["rms4"] < 0.2 * b["rms4"]
-    assert a["rms2"] < 1.1 * b["rms2"]
+    assert a["rms2"] < b["rms2"]
+    # the direct galaxy sum entered training on small mocks, and on held-out small
+    # mocks against it the monopole and hexadecapole residuals fell as well
+    assert meta["direct_seeds"] == [30000, 30199] and meta["direct_rows"] > 0
+    db, da = meta["direct_heldout_before"], meta["direct_heldout_after"]
+    assert da["rms0"] < 0.1 * db["rms0"] and da["rms4"] < 0.3 * db["rms4"]
 
 
 def test_weights_evaluate_on_cpu():
