@@ -84,7 +84,9 @@ def test_autotune_keeps_results():
         plan.assign(g, r)
         before = plan.measure()
         t = plan.autotune(g, r, reps=2)
-        assert all(v > 0 for v in t.tile) and t.yz_grid > 0 and t.ring_lead > 0 and t.measure_ms > 0
+        # a scatter tile, or 0 0 0 for the direct assignment (128^3 interlaced: 16 MB of meshes)
+        assert all(v > 0 for v in t.tile) or all(v == 0 for v in t.tile)
+        assert t.yz_grid > 0 and t.ring_lead > 0 and t.measure_ms > 0
         after_tune = plan.measure()
         plan.assign(g, r)
         after = plan.measure()
