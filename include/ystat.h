@@ -205,7 +205,8 @@ ys_status ys_sum_gal(const ys_config* cfg, const ys_catalog* gal, const ys_catal
  * FFT path; an interlaced pair is averaged (nodes at +H/2 on the second mesh) and,
  * if the plan compensates, the window is divided out.  It is the exact DFT of what
  * the FFT path transforms, at the plan's modes and shells: the two agree shell by
- * shell to float rounding.  Cost: filled nodes x modes (meshes up to ~64^3).
+ * shell to float rounding.  Cost: filled nodes x modes (any mesh, for a few thousand
+ * modes; the nodes go through in chunks of 2^26, with 2 GB of scratch).
  * d_out, d_wedges as for ys_sum_gal.  YS_ERR_STATE before ys_assign.  Synchronous. */
 ys_status ys_sum_grid(ys_plan* plan, double* d_out, double* d_wedges);
 

@@ -126,14 +126,14 @@ __global__ void k_sg_points_cat(const float* __restrict__ x, const float* __rest
   out[i] = q;
 }
 
-// Mesh nodes with F != 0 as points (compacted with a counter).  Node i of mesh j sits
-// at box_min + (i + j/2) H; scale multiplies F (1/2 for each of two interlaced meshes).
-__global__ void k_sg_points_mesh(const float* __restrict__ mesh, int n, int j, double rel_x0, double rel_y0,
-                                 double rel_z0, double H, float scale, unsigned* __restrict__ count,
-                                 SgPoint* __restrict__ out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n3 = (int64_t)n * n * n;
-  if (idx >= n3) return;
+// Mesh nodes [first, first + count) of mesh j with F != 0 as points (compacted with a
+// counter).  Node i of mesh j sits at box_min + (i + j/2) H; scale multiplies F (1/2
+// for each of two interlaced meshes).
+__global__ void k_sg_points_mesh(const float* __restrict__ mesh, int n, int j, int64_t first, int64_t count_nodes,
+                                 double rel_x0, double rel_y0, double rel_z0, double H, float scale,
+                                 unsigned* __restrict__ count, SgPoint* __restrict__ out) {
+  const int64_t idx = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= first + count_nodes) return;
   const float f = mesh[idx];
   if (f == 0.f) return;
   const int iz = (int)(idx % n), iy = (int)((idx / n) % n), ix = (int)(idx / ((int64_t)n * n));
@@ -479,6 +479,9 @@ extern "C" ys_status ys_sum_grid(ys_plan* plan, double* d_out, double* d_wedges)
   const int nmodes = (int)mt.modes.size();
   const bool wedge = d_wedges != nullptr;
   const int64_t n3 = (int64_t)p.n * p.n * p.n;
+  // the nodes go through in chunks of at most 2^26 (2 GB of points), each added into
+  // the FP64 per-mode sums
+  const int64_t chunk = std::min<int64_t>(n3, (int64_t)1 << 26);
   Scratch sc;
   SgMode* d_modes = nullptr;
   double* d_acc = nullptr;
@@ -486,23 +489,23 @@ extern "C" ys_status ys_sum_grid(ys_plan* plan, double* d_out, double* d_wedges)
   unsigned* d_count = nullptr;
   cudaError_t e;
   if ((e = sc.get(d_modes, (size_t)nmodes)) || (e = sc.get(d_acc, (size_t)C_COUNT * 2 * std::max(1, nmodes))) ||
-      (e = sc.get(d_pts, (size_t)(p.m * n3))) || (e = sc.get(d_count, 1)))
+      (e = sc.get(d_pts, (size_t)chunk)) || (e = sc.get(d_count, 1)))
     return fail(e);
   if (nmodes > 0 && (e = cudaMemcpyAsync(d_modes, mt.modes.data(), sizeof(SgMode) * nmodes, cudaMemcpyHostToDevice, st)))
     return fail(e);
-  if ((e = cudaMemsetAsync(d_acc, 0, sizeof(double) * C_COUNT * 2 * std::max(1, nmodes), st)) ||
-      (e = cudaMemsetAsync(d_count, 0, sizeof(unsigned), st)))
-    return fail(e);
+  if ((e = cudaMemsetAsync(d_acc, 0, sizeof(double) * C_COUNT * 2 * std::max(1, nmodes), st))) return fail(e);
   // The interlaced pair is averaged: each mesh's nodes carry F / 2.
   const float scale = p.m == 2 ? 0.5f : 1.f;
-  for (int j = 0; j < p.m; ++j) {
-    k_sg_points_mesh<<<(unsigned)((n3 + 255) / 256), 256, 0, st>>>(
-        p.d_mesh + j * n3, p.n, j, c.box_min[0] - c.observer[0], c.box_min[1] - c.observer[1],
-        c.box_min[2] - c.observer[2], p.H, scale, d_count, d_pts);
-    if ((e = cudaGetLastError())) return fail(e);
-  }
-  if (nmodes > 0 && (e = run_modes(c.ell_max, wedge, d_modes, nmodes, d_pts, d_count, p.m * n3, d_acc, st)))
-    return fail(e);
+  for (int j = 0; j < p.m; ++j)
+    for (int64_t first = 0; first < n3 && nmodes > 0; first += chunk) {
+      const int64_t cnt = std::min(chunk, n3 - first);
+      if ((e = cudaMemsetAsync(d_count, 0, sizeof(unsigned), st))) return fail(e);
+      k_sg_points_mesh<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
+          p.d_mesh + j * n3, p.n, j, first, cnt, c.box_min[0] - c.observer[0], c.box_min[1] - c.observer[1],
+          c.box_min[2] - c.observer[2], p.H, scale, d_count, d_pts);
+      if ((e = cudaGetLastError())) return fail(e);
+      if ((e = run_modes(c.ell_max, wedge, d_modes, nmodes, d_pts, d_count, cnt, d_acc, st))) return fail(e);
+    }
   return finish(mt, d_modes, d_acc, c.compensate ? p.d_invw : nullptr, p.n, p.d_sums, c.alpha, c.n_bins, c.ell_max,
                 wedge, d_out, d_wedges, sc, st);
 }
