@@ -651,7 +651,7 @@ def run_batched(steps, warmup):
     specs, gals, rans = batched_catalogues()
     cfgs = [ys.make_config(mesh, (350.0,) * 3, 500.0, (0.0, 0.0, 0.0), assign="cic", interlace=False, dk=0.01,
                            max_particles=ng + nr) for seed, ng, nr, mesh in specs]
-    batch = ys.Batch(cfgs, branches=4)
+    batch = ys.Batch(cfgs, lanes=8)
     out = torch.zeros((batch.n, batch.stride), dtype=torch.float64, device="cuda")
     t0 = time.perf_counter()
     batch.autotune(gals, rans, reps=2)
@@ -693,7 +693,7 @@ def run_batched(steps, warmup):
     meshes = {m: sum(1 for s_ in specs if s_[3] == m) for m in (128, 192, 256)}
     return {"value": len(specs) / (ms_batch / 1e3), "unit": UNIT, "n_catalogs": len(specs),
             "ms_per_batch": ms_batch, "plain_value": len(specs) / (ms_plain / 1e3),
-            "speedup_vs_plain": ms_plain / ms_batch, "meshes": meshes, "assign": "cic", "branches": 4,
+            "speedup_vs_plain": ms_plain / ms_batch, "meshes": meshes, "assign": "cic", "lanes": 8,
             "autotune_s": tune_s, "rows_with_errors": bad, "seeds": [specs[0][0], specs[-1][0]],
             "particles": int(sum(g + r for s_, g, r, m in specs))}
 
@@ -722,7 +722,7 @@ def run_learned(steps, n_heldout=200):
     cfgs = [ys.make_config(learned.COARSE["n_mesh"], learned.BOX_MIN, learned.BOX_LEN, learned.OBSERVER,
                            assign=learned.COARSE["assign"], interlace=learned.COARSE["interlace"], dk=learned.DK,
                            n_bins=learned.N_BINS, max_particles=c) for c in caps]
-    batch = ys.Batch(cfgs, branches=4)
+    batch = ys.Batch(cfgs, lanes=8)
     rows = torch.zeros((n, batch.stride), dtype=torch.float64, device="cuda")
     corr = torch.empty_like(rows)
     batch.autotune(gals, rans, reps=2)
@@ -773,7 +773,7 @@ def run_learned(steps, n_heldout=200):
             "residual_vs_512": {"uncorrected_128": before, "corrected_128": after,
                                 "definition": "|P_l - P_l(512^3)| / (P_0 + S/I) over shells with modes, "
                                               "k < 0.80 h/Mpc; rms and max"},
-            "coarse": "128^3 CIC, no interlacing, batched (4 branches)",
+            "coarse": "128^3 CIC, no interlacing, batched (waves of 8)",
             "fine": "512^3 TSC, interlaced, plain path",
             "heldout_seeds": [seeds[0], seeds[-1]],
             "trained": {k: meta[k] for k in ("train_seeds", "rows", "steps", "lr", "lr_final")}}

@@ -319,16 +319,24 @@ typedef struct ys_batch_s ys_batch;
 
 /* Many catalogues -- the Sec. 1 use case of hundreds of mocks -- in one graph launch.
  * cfgs[i] configures catalogue i (its max_particles must bound gal_i.n + ran_i.n; its
- * stream is ignored).  Catalogues are spread over `branches` concurrent streams
- * (1..32); each (branch, configuration) pair gets its own plan.  Host-side. */
-ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys_batch** out);
+ * stream is ignored).  Catalogues with the same configuration form a class, measured
+ * in waves of up to `lanes` catalogues (1..32, at most 8 are used): each catalogue of
+ * a wave is assigned on its own plan (lane), then one persistent y,z launch serves
+ * every item of the whole wave through one work queue, one x-stage launch covers all
+ * their pencil blocks and one launch finalizes their rows.  A class with more than
+ * one wave holds up to four sets of min(lanes, its catalogues) plans on their own
+ * streams and sends its waves round them (one wave assigns while another
+ * transforms); the 8 streams are shared out among the classes.  Plans are sized for the class's largest
+ * catalogue.  Host-side. */
+ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t lanes, ys_batch** out);
 
 /* Doubles between consecutive result rows of ys_batch_run: the longest row of the
  * batch (5 n_bins + 5, plus n_bins for l_max = 6 plans). */
 int64_t ys_batch_result_stride(const ys_batch* batch);
 
-/* Autotune every plan of the batch on its largest catalogue (DEVICE pointers,
- * arrays of n).  Synchronous. */
+/* Autotune each class on its largest catalogue (DEVICE pointers, arrays of n): the
+ * launch shapes are chosen on one lane and given to the class's other lanes.
+ * Synchronous. */
 ys_status ys_batch_autotune(ys_batch* batch, const ys_catalog* gal, const ys_catalog* ran, int32_t reps);
 
 /* Run the whole batch.  gal, ran: host arrays of n catalogues holding DEVICE pointers.

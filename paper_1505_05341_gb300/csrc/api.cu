@@ -14,7 +14,7 @@
 
 namespace ys {
 
-template <int N> cudaError_t run_measure_n(Plan& p);
+template <int N> cudaError_t run_measure_n(Plan* const* lanes, int W, double* const* rows);
 template <int N> int yz_grid_n(int ell, cudaError_t* err);
 template <int N> int x_pencils_n();
 template <int N> size_t x_smem_n(int nbins, int nwb, int ell);
@@ -65,9 +65,21 @@ void free_all(Plan& p) {
 
 // Result row: [k_mean | n_modes | p0 | p2 | p4 | alpha, I, S/I, n_out, timeout] and, for
 // l_max = 6, p6 after the five scalars (so rows of l_max <= 4 plans keep their layout).
-__global__ void k_finalize(const double* __restrict__ acc, const double* __restrict__ shell,
-                           const double* __restrict__ sums, const int* __restrict__ flags, double alpha_cfg,
-                           int nbins, int ell, double* __restrict__ res) {
+// One CTA per lane (plans of one configuration measured together); lane l's shell
+// sums, catalogue sums and flag are its own, the shell table is the configuration's.
+struct FinMulti {
+  const double* acc[YZ_MAX_LANES];
+  const double* sums[YZ_MAX_LANES];
+  const int* flags[YZ_MAX_LANES];
+  double* res[YZ_MAX_LANES];
+};
+
+__global__ void k_finalize(const __grid_constant__ FinMulti fm, const double* __restrict__ shell, double alpha_cfg,
+                           int nbins, int ell) {
+  const double* __restrict__ acc = fm.acc[blockIdx.x];
+  const double* __restrict__ sums = fm.sums[blockIdx.x];
+  const int* __restrict__ flags = fm.flags[blockIdx.x];
+  double* __restrict__ res = fm.res[blockIdx.x];
   const double alpha = alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR];
   const double I = alpha * sums[SUM_WR2N];
   const double S = sums[SUM_WG2] + alpha * alpha * sums[SUM_WR2];
@@ -365,10 +377,18 @@ LaunchScope::~LaunchScope() {
   }
 }
 
-cudaError_t launch_finalize(Plan& p) {
+cudaError_t launch_finalize(Plan* const* lanes, int W, double* const* rows) {
+  Plan& p = *lanes[0];
+  FinMulti fm{};
+  for (int l = 0; l < W; ++l) {
+    Plan& q = *lanes[l];
+    fm.acc[l] = q.d_acc;
+    fm.sums[l] = q.d_sums;
+    fm.flags[l] = q.d_sync + 2 * q.m * q.n + 1;
+    fm.res[l] = rows[l];
+  }
   LaunchScope ls(p, 7);
-  k_finalize<<<1, 256, 0, p.stream>>>(p.d_acc, p.d_shell, p.d_sums, p.d_sync + 2 * p.m * p.n + 1, p.cfg.alpha,
-                                      p.cfg.n_bins, p.ell, p.d_result);
+  k_finalize<<<W, 256, 0, p.stream>>>(fm, p.d_shell, p.cfg.alpha, p.cfg.n_bins, p.ell);
   return cudaGetLastError();
 }
 
@@ -398,21 +418,28 @@ int yz_grid_for(Plan& p, cudaError_t* err) {
   }
 }
 
-cudaError_t launch_measure(Plan& p) {
-  switch (p.n) {
-    case 16: return run_measure_n<16>(p);
-    case 32: return run_measure_n<32>(p);
-    case 64: return run_measure_n<64>(p);
-    case 96: return run_measure_n<96>(p);
-    case 128: return run_measure_n<128>(p);
-    case 192: return run_measure_n<192>(p);
-    case 256: return run_measure_n<256>(p);
-    case 384: return run_measure_n<384>(p);
-    case 512: return run_measure_n<512>(p);
-    case 768: return run_measure_n<768>(p);
-    case 1024: return run_measure_n<1024>(p);
+cudaError_t launch_measure_lanes(Plan* const* lanes, int W, double* const* rows) {
+  if (W < 1 || W > YZ_MAX_LANES) return cudaErrorInvalidValue;
+  switch (lanes[0]->n) {
+    case 16: return run_measure_n<16>(lanes, W, rows);
+    case 32: return run_measure_n<32>(lanes, W, rows);
+    case 64: return run_measure_n<64>(lanes, W, rows);
+    case 96: return run_measure_n<96>(lanes, W, rows);
+    case 128: return run_measure_n<128>(lanes, W, rows);
+    case 192: return run_measure_n<192>(lanes, W, rows);
+    case 256: return run_measure_n<256>(lanes, W, rows);
+    case 384: return run_measure_n<384>(lanes, W, rows);
+    case 512: return run_measure_n<512>(lanes, W, rows);
+    case 768: return run_measure_n<768>(lanes, W, rows);
+    case 1024: return run_measure_n<1024>(lanes, W, rows);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_measure(Plan& p) {
+  Plan* lane = &p;
+  double* row = p.d_result;
+  return launch_measure_lanes(&lane, 1, &row);
 }
 
 }  // namespace ys

@@ -2,12 +2,16 @@
 // graph launch.  The paper's motivation is measuring hundreds of mock catalogues
 // (Sec. 1); this is a throughput arrangement of the same per-catalogue steps.
 //
-// Catalogues are spread over B concurrent stream branches by longest-processing-
-// time-first on an estimate of their cost; every (branch, configuration class)
-// owns one plan, reused by that branch's catalogues in sequence.  The whole batch
-// -- assignment, transforms, shell sums and the copy of each result row -- is
-// captured once into a graph and replayed by every ys_batch_run with the same
-// catalogue pointers.
+// Catalogues with the same configuration form a class.  A class owns one to four
+// sets of up to YZ_MAX_LANES plans ("lanes", each with its own meshes, ring and transforms)
+// and is measured in waves: every lane of a set assigns one catalogue, then one
+// persistent y,z launch walks the items of all the wave's catalogues through one
+// ticket queue, one x-stage launch covers all their pencil blocks, and one finalize
+// launch writes each result row straight into the caller's array.  Consecutive waves
+// go round the sets, each on its own stream, so that one wave's assignment overlaps
+// another's transforms; classes run on further streams.
+// The whole batch is captured once into a graph and replayed by every ys_batch_run
+// with the same catalogue pointers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,13 +29,14 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
 }
 
 struct ys_batch_s {
-  int n = 0, branches = 1;
+  int n = 0, lanes = 1;
   std::vector<ys_config> cfgs;
-  std::vector<int> cls;                   // configuration class per catalogue
-  std::vector<int> branch;                // stream branch per catalogue
-  std::vector<std::vector<ys_plan*>> plans;  // [branch][class]
+  std::vector<int> cls;                        // configuration class per catalogue
+  std::vector<std::vector<int>> members;       // catalogues of each class, in order
+  std::vector<std::vector<std::vector<ys_plan*>>> plans;  // [class][set][lane]
+  std::vector<std::vector<int>> set_stream;    // stream index of each class's sets
   std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> events;        // fork + one join per branch
+  std::vector<cudaEvent_t> events;             // fork + one join per stream
   cudaGraphExec_t exec = nullptr;
   std::vector<ys_catalog> captured_gal, captured_ran;
   double* captured_out = nullptr;
@@ -39,6 +44,8 @@ struct ys_batch_s {
 };
 
 namespace {
+
+constexpr int kMaxStreams = 8;
 
 bool same_class(const ys_config& a, const ys_config& b) {
   return a.n_mesh == b.n_mesh && a.box_len == b.box_len && a.box_min[0] == b.box_min[0] &&
@@ -54,9 +61,10 @@ bool same_catalog(const ys_catalog& a, const ys_catalog& b) {
 
 void destroy_batch(ys_batch* b) {
   if (!b) return;
-  for (auto& row : b->plans)
-    for (ys_plan* p : row)
-      if (p) ys_plan_destroy(p);
+  for (auto& sets : b->plans)
+    for (auto& row : sets)
+      for (ys_plan* p : row)
+        if (p) ys_plan_destroy(p);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (cudaStream_t s : b->streams)
     if (s) cudaStreamDestroy(s);
@@ -65,27 +73,50 @@ void destroy_batch(ys_batch* b) {
   delete b;
 }
 
+// Launch shapes tuned on lane 0, given to the class's other lanes.
+void copy_tuning(ys::Plan& dst, const ys::Plan& src) {
+  ys::set_tiles(dst, src.geom.tdim[0], src.geom.tdim[1], src.geom.tdim[2]);
+  dst.direct_assign = src.direct_assign;
+  ys::set_yz_grid(dst, src.yz_grid, src.ring_lead_pct);
+  if (dst.measure_exec) {
+    cudaGraphExecDestroy(dst.measure_exec);
+    dst.measure_exec = nullptr;
+  }
+}
+
 ys_status capture(ys_batch* b, const ys_catalog* gal, const ys_catalog* ran, double* d_out) {
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
   cudaStream_t s0 = b->streams[0];
+  const int ns = (int)b->streams.size();
   cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
   if (e) return YS_ERR_CUDA;
   cudaError_t e2 = cudaEventRecord(b->events[0], s0);
-  for (int br = 1; br < b->branches && !e2; ++br) e2 = cudaStreamWaitEvent(b->streams[br], b->events[0], 0);
-  for (int i = 0; i < b->n && !e2; ++i) {
-    ys::Plan& p = b->plans[b->branch[i]][b->cls[i]]->p;
-    e2 = ys::launch_assign(p, gal[i], ran[i]);
-    if (!e2) e2 = ys::launch_measure(p);
-    if (!e2)
-      e2 = cudaMemcpyAsync(d_out + (size_t)i * b->stride, p.d_result, sizeof(double) * p.row_len,
-                           cudaMemcpyDeviceToDevice, p.stream);
+  for (int s = 1; s < ns && !e2; ++s) e2 = cudaStreamWaitEvent(b->streams[s], b->events[0], 0);
+  for (size_t c = 0; c < b->members.size() && !e2; ++c) {
+    const std::vector<int>& mem = b->members[c];
+    const int nsets = (int)b->plans[c].size();
+    const int W = (int)b->plans[c][0].size();
+    int wave = 0;
+    for (size_t w0 = 0; w0 < mem.size() && !e2; w0 += W, ++wave) {
+      const int w = (int)std::min<size_t>(W, mem.size() - w0);
+      const std::vector<ys_plan*>& set = b->plans[c][wave % nsets];
+      ys::Plan* lanes[ys::YZ_MAX_LANES];
+      double* rows[ys::YZ_MAX_LANES];
+      for (int l = 0; l < w && !e2; ++l) {
+        const int i = mem[w0 + l];
+        lanes[l] = &set[l]->p;
+        rows[l] = d_out + (size_t)i * b->stride;
+        e2 = ys::launch_assign(*lanes[l], gal[i], ran[i]);
+      }
+      if (!e2) e2 = ys::launch_measure_lanes(lanes, w, rows);
+    }
   }
-  for (int br = 1; br < b->branches && !e2; ++br) {
-    e2 = cudaEventRecord(b->events[br], b->streams[br]);
-    if (!e2) e2 = cudaStreamWaitEvent(s0, b->events[br], 0);
+  for (int s = 1; s < ns && !e2; ++s) {
+    e2 = cudaEventRecord(b->events[s], b->streams[s]);
+    if (!e2) e2 = cudaStreamWaitEvent(s0, b->events[s], 0);
   }
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(s0, &graph);
@@ -107,17 +138,17 @@ ys_status capture(ys_batch* b, const ys_catalog* gal, const ys_catalog* ran, dou
 
 extern "C" {
 
-ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys_batch** out) {
-  if (!cfgs || !out || n <= 0 || branches <= 0 || branches > 32) return YS_ERR_ARG;
+ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t lanes, ys_batch** out) {
+  if (!cfgs || !out || n <= 0 || lanes <= 0 || lanes > 32) return YS_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < n; ++i)
     if (cfgs[i].max_particles <= 0) return YS_ERR_ARG;  // capacity must be known before capture
   ys_batch* b = new (std::nothrow) ys_batch;
   if (!b) return YS_ERR_OOM;
   b->n = n;
-  b->branches = std::min<int>(branches, n);
+  b->lanes = std::min<int>(lanes, ys::YZ_MAX_LANES);
   b->cfgs.assign(cfgs, cfgs + n);
-  // configuration classes
+  // configuration classes, each with its catalogues in input order
   std::vector<int> reps;  // first catalogue of each class
   b->cls.resize(n);
   for (int i = 0; i < n; ++i) {
@@ -127,52 +158,60 @@ ys_status ys_batch_create(const ys_config* cfgs, int32_t n, int32_t branches, ys
     if (c < 0) {
       c = (int)reps.size();
       reps.push_back(i);
+      b->members.emplace_back();
     }
     b->cls[i] = c;
+    b->members[c].push_back(i);
   }
-  // longest-processing-time-first over the branches (cost ~ N^3 log N + particles)
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  auto cost = [&](int i) {
-    const double N = cfgs[i].n_mesh;
-    return N * N * N * std::log2(N) * (cfgs[i].interlace ? 2.0 : 1.0) + 40.0 * (double)cfgs[i].max_particles;
-  };
-  std::sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
-  std::vector<double> load(b->branches, 0.0);
-  b->branch.resize(n);
-  for (int i : order) {
-    const int br = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    b->branch[i] = br;
-    load[br] += cost(i);
+  const int nclass = (int)reps.size();
+  // lane sets per class (each on its own stream): as many as its waves, the streams
+  // shared out among the classes and at most 4
+  const int W = b->lanes;
+  std::vector<int> nsets(nclass);
+  int want = 0;
+  for (int c = 0; c < nclass; ++c) {
+    const int waves = ((int)b->members[c].size() + W - 1) / W;
+    nsets[c] = std::max(1, std::min({waves, kMaxStreams / std::max(1, nclass), 4}));
+    want += nsets[c];
   }
-  b->streams.assign(b->branches, nullptr);
-  b->events.assign(b->branches, nullptr);
-  for (int br = 0; br < b->branches; ++br) {
-    if (cudaStreamCreateWithFlags(&b->streams[br], cudaStreamNonBlocking) ||
-        cudaEventCreateWithFlags(&b->events[br], cudaEventDisableTiming)) {
+  const int ns = std::min(want, kMaxStreams);
+  b->streams.assign(ns, nullptr);
+  b->events.assign(ns, nullptr);
+  for (int s = 0; s < ns; ++s) {
+    if (cudaStreamCreateWithFlags(&b->streams[s], cudaStreamNonBlocking) ||
+        cudaEventCreateWithFlags(&b->events[s], cudaEventDisableTiming)) {
       destroy_batch(b);
       return YS_ERR_CUDA;
     }
   }
-  // one plan per (branch, class) that has catalogues, sized for its largest one
-  b->plans.assign(b->branches, std::vector<ys_plan*>(reps.size(), nullptr));
-  int row_max = 0;
-  for (int br = 0; br < b->branches; ++br)
-    for (size_t c = 0; c < reps.size(); ++c) {
-      int64_t cap = 0;
-      for (int i = 0; i < n; ++i)
-        if (b->branch[i] == br && b->cls[i] == (int)c) cap = std::max<int64_t>(cap, cfgs[i].max_particles);
-      if (cap == 0) continue;
+  // each set of each class on a stream (round robin) with min(lanes, its catalogues)
+  // plans, each sized for the class's largest catalogue
+  b->set_stream.assign(nclass, {});
+  b->plans.assign(nclass, {});
+  int row_max = 0, next_stream = 0;
+  for (int c = 0; c < nclass; ++c) {
+    int64_t cap = 0;
+    for (int i : b->members[c]) cap = std::max<int64_t>(cap, cfgs[i].max_particles);
+    const int Wc = std::min<int>(W, (int)b->members[c].size());
+    b->plans[c].assign(nsets[c], {});
+    for (int k = 0; k < nsets[c]; ++k) {
+      const int sidx = next_stream++ % ns;
+      b->set_stream[c].push_back(sidx);
       ys_config cc = cfgs[reps[c]];
       cc.max_particles = cap;
-      cc.stream = b->streams[br];
-      ys_status st = ys_plan_create(&cc, &b->plans[br][c]);
-      if (st != YS_OK) {
-        destroy_batch(b);
-        return st;
+      cc.stream = b->streams[sidx];
+      for (int l = 0; l < Wc; ++l) {
+        ys_plan* pl = nullptr;
+        ys_status st = ys_plan_create(&cc, &pl);
+        if (st != YS_OK) {
+          destroy_batch(b);
+          return st;
+        }
+        b->plans[c][k].push_back(pl);
+        row_max = std::max(row_max, pl->p.row_len);
       }
-      row_max = std::max(row_max, b->plans[br][c]->p.row_len);
     }
+  }
   b->stride = row_max;
   *out = b;
   return YS_OK;
@@ -182,23 +221,22 @@ int64_t ys_batch_result_stride(const ys_batch* batch) { return batch ? batch->st
 
 ys_status ys_batch_autotune(ys_batch* b, const ys_catalog* gal, const ys_catalog* ran, int32_t reps) {
   if (!b || !gal || !ran) return YS_ERR_ARG;
-  for (int br = 0; br < b->branches; ++br)
-    for (size_t c = 0; c < b->plans[br].size(); ++c) {
-      ys_plan* pl = b->plans[br][c];
-      if (!pl) continue;
-      // tune on the largest catalogue of this plan
-      int pick = -1;
-      for (int i = 0; i < b->n; ++i)
-        if (b->branch[i] == br && b->cls[i] == (int)c &&
-            (pick < 0 || gal[i].n + ran[i].n > gal[pick].n + ran[pick].n))
-          pick = i;
-      std::string why;
-      ys_status st = ys::autotune(pl->p, gal[pick], ran[pick], reps, nullptr, why);
-      if (st != YS_OK) {
-        ys::g_last_cuda_error = why;
-        return st;
-      }
+  for (size_t c = 0; c < b->plans.size(); ++c) {
+    // tune lane 0 on the class's largest catalogue; the other lanes take its shapes
+    int pick = -1;
+    for (int i : b->members[c])
+      if (pick < 0 || gal[i].n + ran[i].n > gal[pick].n + ran[pick].n) pick = i;
+    std::string why;
+    ys::Plan& p0 = b->plans[c][0][0]->p;
+    ys_status st = ys::autotune(p0, gal[pick], ran[pick], reps, nullptr, why);
+    if (st != YS_OK) {
+      ys::g_last_cuda_error = why;
+      return st;
     }
+    for (auto& set : b->plans[c])
+      for (ys_plan* pl : set)
+        if (&pl->p != &p0) copy_tuning(pl->p, p0);
+  }
   for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
   if (b->exec) {  // launch shapes changed
     cudaGraphExecDestroy(b->exec);
@@ -220,9 +258,10 @@ ys_status ys_batch_run(ys_batch* b, const ys_catalog* gal, const ys_catalog* ran
   if (!same) {
     ys_status st = capture(b, gal, ran, d_results);
     if (st != YS_OK) return st;
-    for (auto& row : b->plans)
-      for (ys_plan* p : row)
-        if (p) p->p.assigned = true;
+    for (auto& sets : b->plans)
+      for (auto& row : sets)
+        for (ys_plan* p : row)
+          if (p) p->p.assigned = true;
   }
   cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
   if (e) {

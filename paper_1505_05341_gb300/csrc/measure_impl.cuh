@@ -7,7 +7,7 @@
 
 namespace ys {
 
-cudaError_t launch_finalize(Plan& p);
+cudaError_t launch_finalize(Plan* const* lanes, int W, double* const* rows);
 
 // CTAs of the persistent y,z kernel that fit on the device at once.
 template <int N, int ELL>
@@ -39,39 +39,53 @@ int yz_grid_n(int ell, cudaError_t* err) {
   }
 }
 
+// The launches below take the lanes (plans of one configuration, each with its own
+// catalogue already assigned) measured together; a single plan is one lane.  Work is
+// queued on lane 0's stream.
 template <int N, int ELL>
-cudaError_t run_yz(Plan& p) {
+cudaError_t run_yz(Plan* const* lanes, int W) {
   using Y = YZ<N, ELL>;
+  Plan& p0 = *lanes[0];
   cudaError_t err;
-  if ((err = cudaMemsetAsync(p.d_sync, 0, sizeof(int) * (2 * p.m * N + 2), p.stream))) return err;
-  YZParams prm;
-  prm.mesh = p.d_mesh;
-  prm.rel = p.d_rel;
-  prm.tw = p.d_tw;
-  prm.ring = p.d_z;
-  prm.gout = p.d_g;
-  prm.col_off = p.d_col_off;
-  prm.done_z = p.d_sync;
-  prm.done_y = p.d_sync + p.m * N;
-  prm.ticket = p.d_sync + 2 * p.m * N;
-  prm.err = p.d_sync + 2 * p.m * N + 1;
-  prm.nzc = p.nzc;
-  prm.np = p.np_pad;
-  prm.m = p.m;
-  prm.S = p.ring_slots;
-  prm.D = p.ring_lead;
-  prm.spin_limit = p.yz_wait_ns;  // 1 s unless a test shortened it; then the kernel reports a timeout
-  prm.skip_plane = p.fault_skip_plane;
+  YZMulti pm{};
+  int items = 0;
+  for (int l = 0; l < W; ++l) {
+    Plan& p = *lanes[l];
+    if ((err = cudaMemsetAsync(p.d_sync, 0, sizeof(int) * (2 * p.m * N + 2), p0.stream))) return err;
+    YZParams& prm = pm.lane[l];
+    prm.mesh = p.d_mesh;
+    prm.rel = p.d_rel;
+    prm.tw = p.d_tw;
+    prm.ring = p.d_z;
+    prm.gout = p.d_g;
+    prm.col_off = p.d_col_off;
+    prm.done_z = p.d_sync;
+    prm.done_y = p.d_sync + p.m * N;
+    prm.ticket = p.d_sync + 2 * p.m * N;
+    prm.err = p.d_sync + 2 * p.m * N + 1;
+    prm.nzc = p.nzc;
+    prm.np = p.np_pad;
+    prm.m = p.m;
+    prm.S = p.ring_slots;
+    prm.D = p.ring_lead;
+    prm.spin_limit = p.yz_wait_ns;  // 1 s unless a test shortened it; then the kernel reports a timeout
+    prm.skip_plane = p.fault_skip_plane;
+    items += (p.m * N + p.ring_lead) * (N / Y::R + p.nzc);
+    pm.end[l] = items;
+  }
+  pm.nlanes = W;
+  pm.ticket = p0.d_sync + 2 * p0.m * N;
   if ((err = cudaFuncSetAttribute(k_yz<N, ELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Y::smem)))
     return err;
-  LaunchScope ls(p, 4);
-  k_yz<N, ELL><<<p.yz_grid, Y::THREADS, Y::smem, p.stream>>>(prm);
+  LaunchScope ls(p0, 4);
+  k_yz<N, ELL><<<p0.yz_grid, Y::THREADS, Y::smem, p0.stream>>>(pm);
   return cudaGetLastError();
 }
 
 template <int N, int ELL, int M>
-cudaError_t run_x(Plan& p) {
+cudaError_t run_x(Plan* const* lanes, int W) {
   using XC = XCombine<N, ELL, M>;
+  Plan& p = *lanes[0];
   const int nbins = p.cfg.n_bins;
   cudaError_t err;
   int dev0 = 0, smem_max = 0;
@@ -112,12 +126,20 @@ cudaError_t run_x(Plan& p) {
   int dev = 0, sms = 0;
   if ((err = cudaGetDevice(&dev))) return err;
   if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return err;
+  XMulti pm{};
+  for (int l = 0; l < W; ++l) {
+    pm.map[l] = lanes[l]->gmap;
+    pm.acc[l] = lanes[l]->d_acc;
+    pm.err[l] = lanes[l]->d_sync + 2 * lanes[l]->m * N + 1;
+  }
+  pm.nlanes = W;
+  // the resident CTAs are shared among the lanes
   const int npb = p.np_pad / XC::P;
-  const int grid = std::max(1, std::min(npb, std::max(1, per) * sms));
+  const int resident = std::max(1, per) * sms;
+  const int grid = std::max(1, std::min(npb, (resident + W - 1) / W));
   LaunchScope ls(p, 6);
-  k_x_combine<N, ELL, M><<<grid, XC::THREADS, smem, p.stream>>>(p.gmap, p.np_pad, p.d_pencil, p.d_tw, p.d_invw,
-                                                                 p.d_phase, p.d_lut, p.n2_hi, p.d_acc, nbins, nwb,
-                                                                 p.d_sync + 2 * p.m * N + 1);
+  k_x_combine<N, ELL, M><<<dim3(grid, W), XC::THREADS, smem, p.stream>>>(pm, p.np_pad, p.d_pencil, p.d_tw, p.d_invw,
+                                                                         p.d_phase, p.d_lut, p.n2_hi, nbins, nwb);
   return cudaGetLastError();
 }
 
@@ -133,33 +155,36 @@ size_t x_smem_n(int nbins, int nwb, int ell) {
 }
 
 template <int N, int ELL>
-cudaError_t run_ell(Plan& p) {
+cudaError_t run_ell(Plan* const* lanes, int W) {
   cudaError_t err;
-  if (p.np > 0) {
-    if ((err = run_yz<N, ELL>(p))) return err;
-    if ((err = (p.m == 2 ? run_x<N, ELL, 2>(p) : run_x<N, ELL, 1>(p)))) return err;
+  if (lanes[0]->np > 0) {
+    if ((err = run_yz<N, ELL>(lanes, W))) return err;
+    if ((err = (lanes[0]->m == 2 ? run_x<N, ELL, 2>(lanes, W) : run_x<N, ELL, 1>(lanes, W)))) return err;
   }
   return cudaSuccess;
 }
 
+// Measurement of W lanes of one configuration; lane l's result row goes to rows[l].
 template <int N>
-cudaError_t run_measure_n(Plan& p) {
+cudaError_t run_measure_n(Plan* const* lanes, int W, double* const* rows) {
   cudaError_t err;
-  if ((err = cudaMemsetAsync(p.d_acc, 0, sizeof(double) * 4 * p.cfg.n_bins, p.stream))) return err;
-  switch (p.ell) {
-    case 0: err = run_ell<N, 0>(p); break;
-    case 2: err = run_ell<N, 2>(p); break;
-    case 4: err = run_ell<N, 4>(p); break;
+  Plan& p0 = *lanes[0];
+  for (int l = 0; l < W; ++l)
+    if ((err = cudaMemsetAsync(lanes[l]->d_acc, 0, sizeof(double) * 4 * p0.cfg.n_bins, p0.stream))) return err;
+  switch (p0.ell) {
+    case 0: err = run_ell<N, 0>(lanes, W); break;
+    case 2: err = run_ell<N, 2>(lanes, W); break;
+    case 4: err = run_ell<N, 4>(lanes, W); break;
     case 6:
       if constexpr (ell6_supported<N>()) {
-        err = run_ell<N, 6>(p);
+        err = run_ell<N, 6>(lanes, W);
         break;
       }
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
   if (err) return err;
-  return launch_finalize(p);
+  return launch_finalize(lanes, W, rows);
 }
 
 }  // namespace ys

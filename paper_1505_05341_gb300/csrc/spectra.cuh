@@ -97,6 +97,18 @@ struct YZParams {
   int skip_plane;        // >= 0: that plane's row items withhold their completion (test hook)
 };
 
+// Several catalogues of one configuration ("lanes", each with its own mesh, ring,
+// counters, error flag and grouped output) in one launch: the ticket queue runs
+// through lane 0's items, then lane 1's, and so on (end[l] = items of lanes 0..l).
+// Items of different lanes never wait on each other, so the argument above holds
+// lane by lane.  A single plan is the one-lane case.
+struct YZMulti {
+  YZParams lane[YZ_MAX_LANES];
+  int end[YZ_MAX_LANES];
+  int nlanes;
+  int* ticket;
+};
+
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -327,7 +339,7 @@ __device__ __forceinline__ void signal_release(int* counter) {
 }
 
 template <int N, int ELL>
-__global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(YZParams prm) {
+__global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid_constant__ YZMulti pm) {
   using Y = YZ<N, ELL>;
   constexpr int R = Y::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -336,20 +348,25 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(YZParams prm
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* nodes = tw + N;
   float2* work = nodes + (Y::smem_nodes / sizeof(float2));
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = prm.tw[k];
-  const int NZ = N / R, NY = prm.nzc, IPS = NZ + NY;
-  const int mN = prm.m * N;
-  const int total = (mN + prm.D) * IPS;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = pm.lane[0].tw[k];  // same N: same twiddles
+  const int NZ = N / R;
+  const int total = pm.end[pm.nlanes - 1];
   const size_t n3 = (size_t)N * N * N;
-  const size_t slot_elems = (size_t)Y::NB * prm.nzc * N;
   __syncthreads();
   for (;;) {
     // One ticket at a time: a claimed item must start at once, since later items
     // may depend on it.
-    if (threadIdx.x == 0) s_item = atomicAdd(prm.ticket, 1);
+    if (threadIdx.x == 0) s_item = atomicAdd(pm.ticket, 1);
     __syncthreads();
-    const int item = s_item;
-    if (item >= total) break;
+    const int gitem = s_item;
+    if (gitem >= total) break;
+    int l = 0;
+    while (gitem >= pm.end[l]) ++l;
+    const YZParams& prm = pm.lane[l];
+    const int item = gitem - (l > 0 ? pm.end[l - 1] : 0);
+    const int NY = prm.nzc, IPS = NZ + NY;
+    const int mN = prm.m * N;
+    const size_t slot_elems = (size_t)Y::NB * prm.nzc * N;
     const int step = item / IPS, sub = item - step * IPS;
     if (sub < NZ) {
       const int p = step;  // row item of plane p
@@ -383,6 +400,16 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(YZParams prm
 
 // Pencils per CTA of k_x_combine.
 __host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 512 ? 4 : 8); }
+
+// The x stage of several lanes (catalogues of one configuration, as for k_yz) in one
+// launch: grid (blocks per lane, lanes); the tables (pencils, twiddles, window, phases,
+// shell lookup) are the configuration's and the same for every lane.
+struct XMulti {
+  CUtensorMap map[YZ_MAX_LANES];
+  double* acc[YZ_MAX_LANES];
+  int* err[YZ_MAX_LANES];
+  int nlanes;
+};
 
 // First group of the multipole that group g belongs to (groups: A_0 | l = 2, powers
 // 0..2 of k_x | l = 4, powers 0..4 | l = 6, powers 0..6), and its last.
@@ -501,10 +528,13 @@ struct XCombine {
 
 template <int N, int ELL, int M>
 __global__ void __launch_bounds__(XCombine<N, ELL, M>::THREADS, XCombine<N, ELL, M>::MIN_BLOCKS)
-k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* __restrict__ pencil,
+k_x_combine(const __grid_constant__ XMulti pm, int np_pad, const short2* __restrict__ pencil,
             const float2* __restrict__ tw_g, const float* __restrict__ invw_g, const float2* __restrict__ phase_g,
-            const short* __restrict__ lut, int n2_hi, double* __restrict__ acc, int nbins, int nwb,
-            int* __restrict__ err) {
+            const short* __restrict__ lut, int n2_hi, int nbins, int nwb) {
+  // lane blockIdx.y: its grouped transforms (tensor map), shell accumulators, error flag
+  const CUtensorMap* gmap = &pm.map[blockIdx.y];
+  double* __restrict__ acc = pm.acc[blockIdx.y];
+  int* __restrict__ err = pm.err[blockIdx.y];
   using XC = XCombine<N, ELL, M>;
   constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, TILES = XC::TILES, RL = XC::RL;
   constexpr bool HORNER = x_horner<N, ELL>();
@@ -547,7 +577,7 @@ k_x_combine(const __grid_constant__ CUtensorMap gmap, int np_pad, const short2* 
     mbar_expect_tx(&bar[s & 1], XC::TILE_BYTES);
 #pragma unroll
     for (int bx = 0; bx < XC::BOXES; ++bx)
-      tma_load_2d(dst + bx * XC::BOX_ROWS * P, &gmap, pb * P * 2, (mj * XC::NG + gi) * N + bx * XC::BOX_ROWS, &bar[s & 1]);
+      tma_load_2d(dst + bx * XC::BOX_ROWS * P, gmap, pb * P * 2, (mj * XC::NG + gi) * N + bx * XC::BOX_ROWS, &bar[s & 1]);
   };
   if (tid == 0 && total > 0) issue(0);
   const int p = tid % P, tl = tid / P;

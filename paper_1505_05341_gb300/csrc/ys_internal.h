@@ -27,6 +27,9 @@ enum SumSlot {
 // default and the shapes the autotuner tries (each divides every supported N once
 // capped; shared memory = meshes x nodes x 4 bytes).
 constexpr int TILE_X = 16, TILE_Y = 16, TILE_Z = 32;
+
+// Most catalogues of one configuration measured in one set of spectral launches.
+constexpr int YZ_MAX_LANES = 8;
 constexpr int kTileCandidates[5][3] = {{16, 16, 32}, {8, 16, 32}, {16, 16, 16}, {32, 16, 32}, {8, 8, 32}};
 
 struct Geom {
@@ -145,6 +148,10 @@ ys_status ensure_particles(Plan& p, int64_t total);
 inline int result_row_len(int nbins, int ell) { return 5 * nbins + 5 + (ell >= 6 ? nbins : 0); }
 extern thread_local std::string g_last_cuda_error;
 cudaError_t launch_measure(Plan& p);
+// The measurement of W <= 8 plans of one configuration (each already assigned) in one
+// y,z launch, one x-stage launch and one finalize launch; lane l's result row goes to
+// rows[l].  Queued on lanes[0]'s stream.
+cudaError_t launch_measure_lanes(Plan* const* lanes, int W, double* const* rows);
 ys_status assign_noalloc(Plan& p, const ys_catalog& gal, const ys_catalog& ran, std::string& why);
 
 }  // namespace ys

@@ -377,14 +377,15 @@ class Plan:
 
 
 class Batch:
-    """ys_batch: many catalogues (mixed configurations) in one graph launch."""
+    """ys_batch: many catalogues (mixed configurations) in one graph launch, measured in
+    waves of up to `lanes` catalogues per configuration."""
 
-    def __init__(self, configs, branches=4):
+    def __init__(self, configs, lanes=8):
         lib = _lib()
         n = len(configs)
         arr = (YsConfig * n)(*configs)
         h = ctypes.c_void_p()
-        _check(lib.ys_batch_create(arr, n, branches, ctypes.byref(h)), "ys_batch_create")
+        _check(lib.ys_batch_create(arr, n, lanes, ctypes.byref(h)), "ys_batch_create")
         self._h = h
         self.n = n
         self.n_bins = [c.n_bins for c in configs]

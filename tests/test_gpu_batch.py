@@ -51,7 +51,7 @@ def test_batch_rows_equal_single_runs_and_oracle():
     cats, cfgs = batch_inputs()
     gals = [dev(c[0]) for c in cats]
     rans = [dev(c[1]) for c in cats]
-    with ys.Batch(cfgs, branches=3) as batch:
+    with ys.Batch(cfgs, lanes=3) as batch:
         out = torch.zeros((batch.n, batch.stride), dtype=torch.float64, device="cuda")
         batch.run(gals, rans, out)
         torch.cuda.synchronize()
@@ -93,3 +93,35 @@ def test_autotune_keeps_results():
     # other tiles and grids add the same terms in another order: twice the parity bar
     close_rows(before, after_tune, "autotune state", 2 * TOL)
     close_rows(before, after, "after autotune", 2 * TOL)
+
+
+def test_waves_of_lanes_equal_single_runs_and_oracle():
+    """Twelve catalogues of one configuration measured in waves of 5, 5 and 2 lanes: the
+    persistent y,z launch serves all of a wave's items through one work queue, and the
+    x stage and finalize cover all its catalogues. Every row matches the oracle and a
+    single-plan run of its catalogue (two float evaluations: twice the bar)."""
+    n = 64
+    cats, cfgs = [], []
+    for i in range(12):
+        ng = 4000 + 700 * i
+        gal, ran, geo = synth.poisson_cube(ng, 5 * ng, side=800.0, center=(400.0, 100.0, -200.0), seed=500 + i)
+        cfgs.append(ys.make_config(n, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True,
+                                   dk=0.01, max_particles=6 * 4000 + 6 * 700 * 11))
+        cats.append((gal, ran, geo))
+    gals = [dev(c[0]) for c in cats]
+    rans = [dev(c[1]) for c in cats]
+    with ys.Batch(cfgs, lanes=5) as batch:
+        out = torch.zeros((batch.n, batch.stride), dtype=torch.float64, device="cuda")
+        batch.autotune(gals, rans, reps=1)
+        batch.run(gals, rans, out)
+        torch.cuda.synchronize()
+        rows = batch.results(out)
+    geo = cats[0][2]
+    bins = BinSpec.up_to(np.pi * n / geo.box_len, 0.01)
+    with ys.Plan(n, geo.box_min, geo.box_len, geo.observer, assign="tsc", interlace=True, dk=0.01) as plan:
+        for i, (gal, ran, geo_i) in enumerate(cats):
+            plan.assign(gals[i], rans[i])
+            single = plan.measure()
+            ref = oracle.fft_multipoles(gal, ran, geo_i, n, bins, assign="tsc", interlace=True)
+            compare(rows[i], ref, 4, f"wave lane row {i}")
+            close_rows(single, rows[i], f"wave lane row {i} vs single", 2 * TOL)
