@@ -446,7 +446,8 @@ def run_ours(args):
                    "n_gal": gal.n, "n_ran": ran.n, "k_max": K_MAX, "dk": DK, "fields": "1+6+15",
                    "l2": "inputs larger than L2 (0.96 GB catalogue, 1 GB meshes, 11 GB spectra)",
                    "parallelism": f"replicas{world}", "seeds": seeds_record(rank, args.workload),
-                   "tuned": ({"tile": list(tuning.tile), "yz_grid": tuning.yz_grid, "ring_lead": tuning.ring_lead}
+                   "tuned": ({"tile": list(tuning.tile), "yz_grid": tuning.yz_grid, "ring_lead": tuning.ring_lead,
+                              "x_pencils": tuning.x_pencils}
                              if tuning is not None else "defaults (--no-tune)")},
         "roofline": roofline,
         "step_roofline": {"bound": "hbm", "alg_bytes": b_alg, "achieved_GBps": b_alg / (ms_step / 1e3) / 1e9,

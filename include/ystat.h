@@ -288,20 +288,22 @@ ys_status ys_plan_destroy(ys_plan* plan);
  * paper's equations, which these calls evaluate unchanged) ---- */
 
 /* Launch shapes the autotuner chose: scatter tile (nodes per axis; 0 0 0 = the direct
- * assignment, see ys_plan_set_direct_assign), CTAs of the persistent y,z kernel and
- * the lead (in x-planes) of its column items over its row items, with the best
- * measured times. */
+ * assignment, see ys_plan_set_direct_assign), CTAs of the persistent y,z kernel, the
+ * lead (in x-planes) of its column items over its row items, and the x stage's FFT
+ * tile (pencils transformed together by one CTA), with the best measured times. */
 typedef struct {
   int32_t tile[3];
   int32_t yz_grid;
   int32_t ring_lead;
   double assign_ms;
   double measure_ms;
+  int32_t x_pencils;
 } ys_tuning;
 
 /* Time the candidate scatter tiles (16x16x32, 8x16x32, 16x16x16, 32x16x32, 8x8x32)
  * and, for small meshes, the direct assignment; then the y,z grids (resident, 3/4,
- * 1/2) and ring leads (0.7x, 1x, 1.4x, 2x a work-balanced estimate) on this catalogue
+ * 1/2), ring leads (0.7x, 1x, 1.4x, 2x a work-balanced estimate) and x-stage tiles
+ * (the mesh's default pencils per CTA and half or twice that) on this catalogue
  * (DEVICE pointers), reps timed calls each, and keep the fastest in the plan.  Leaves
  * the catalogue assigned.  Synchronous.  out may be NULL. */
 ys_status ys_plan_autotune(ys_plan* plan, const ys_catalog* gal, const ys_catalog* ran, int32_t reps,

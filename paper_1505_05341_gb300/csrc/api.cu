@@ -16,7 +16,6 @@ namespace ys {
 
 template <int N> cudaError_t run_measure_n(Plan* const* lanes, int W, double* const* rows);
 template <int N> int yz_grid_n(int ell, cudaError_t* err);
-template <int N> int x_pencils_n();
 template <int N> size_t x_smem_n(int nbins, int nwb, int ell);
 
 thread_local std::string g_last_cuda_error;
@@ -114,22 +113,6 @@ __global__ void k_finalize(const __grid_constant__ FinMulti fm, const double* __
   }
 }
 
-int x_pencils_for(int n) {
-  switch (n) {
-    case 16: return x_pencils_n<16>();
-    case 32: return x_pencils_n<32>();
-    case 64: return x_pencils_n<64>();
-    case 96: return x_pencils_n<96>();
-    case 128: return x_pencils_n<128>();
-    case 192: return x_pencils_n<192>();
-    case 256: return x_pencils_n<256>();
-    case 384: return x_pencils_n<384>();
-    case 512: return x_pencils_n<512>();
-    case 768: return x_pencils_n<768>();
-    default: return x_pencils_n<1024>();
-  }
-}
-
 size_t x_smem_for(int n, int nbins, int nwb, int ell) {
   switch (n) {
     case 16: return x_smem_n<16>(nbins, nwb, ell);
@@ -161,7 +144,7 @@ ys_status make_gmap(Plan& p) {
                                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                               CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                               CUtensorMapFloatOOBfill)>(fn);
-  const int P = x_pencils_for(p.n);
+  const int P = p.x_pencils;
   const cuuint64_t dims[2] = {(cuuint64_t)2 * p.np_pad, (cuuint64_t)p.m * p.ng * p.n};
   const cuuint64_t strides[1] = {(cuuint64_t)2 * p.np_pad * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)(2 * P), (cuuint32_t)x_box_rows(p.n)};
@@ -175,6 +158,30 @@ ys_status make_gmap(Plan& p) {
   }
   return YS_OK;
 }
+
+}  // namespace
+
+ys_status set_x_pencils(Plan& p, int pencils) {
+  if (pencils != k3_pencils(p.n) && pencils != k3_pencils_alt(p.n)) return YS_ERR_ARG;
+  if (pencils == p.x_pencils) return YS_OK;
+  const int old = p.x_pencils;
+  p.x_pencils = pencils;
+  if (p.np > 0) {
+    ys_status st = make_gmap(p);
+    if (st != YS_OK) {
+      p.x_pencils = old;
+      make_gmap(p);
+      return st;
+    }
+  }
+  if (p.measure_exec) {
+    cudaGraphExecDestroy(p.measure_exec);
+    p.measure_exec = nullptr;
+  }
+  return YS_OK;
+}
+
+namespace {
 
 // FP64 host tables (shells, pencils, windows, phases, twiddles, node positions).
 ys_status build_tables(Plan& p) {
@@ -212,8 +219,10 @@ ys_status build_tables(Plan& p) {
   }
   p.nzc = nzc;
   p.np = (int)pen.size();
-  // pad to whole x-stage pencil blocks with pencils that match no shell (k_z = -1)
-  const int xp = x_pencils_for(n);
+  // pad to whole x-stage pencil blocks of either size with pencils that match no
+  // shell (k_z = -1)
+  const int xp = std::max(k3_pencils(n), k3_pencils_alt(n));
+  p.x_pencils = k3_pencils(n);
   p.np_pad = std::max(xp, (p.np + xp - 1) / xp * xp);
   while ((int)pen.size() < p.np_pad) pen.push_back(make_short2(0, -1));
   // mode count and sum |k| per shell (half grid, weight 2 for 0 < k_z < n/2)

@@ -78,6 +78,7 @@ void copy_tuning(ys::Plan& dst, const ys::Plan& src) {
   ys::set_tiles(dst, src.geom.tdim[0], src.geom.tdim[1], src.geom.tdim[2]);
   dst.direct_assign = src.direct_assign;
   ys::set_yz_grid(dst, src.yz_grid, src.ring_lead_pct);
+  ys::set_x_pencils(dst, src.x_pencils);
   if (dst.measure_exec) {
     cudaGraphExecDestroy(dst.measure_exec);
     dst.measure_exec = nullptr;

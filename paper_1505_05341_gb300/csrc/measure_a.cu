@@ -3,18 +3,14 @@
 namespace ys {
 template cudaError_t run_measure_n<16>(Plan* const*, int, double* const*);
 template int yz_grid_n<16>(int, cudaError_t*);
-template int x_pencils_n<16>();
 template size_t x_smem_n<16>(int, int, int);
 template cudaError_t run_measure_n<32>(Plan* const*, int, double* const*);
 template int yz_grid_n<32>(int, cudaError_t*);
-template int x_pencils_n<32>();
 template size_t x_smem_n<32>(int, int, int);
 template cudaError_t run_measure_n<64>(Plan* const*, int, double* const*);
 template int yz_grid_n<64>(int, cudaError_t*);
-template int x_pencils_n<64>();
 template size_t x_smem_n<64>(int, int, int);
 template cudaError_t run_measure_n<96>(Plan* const*, int, double* const*);
 template int yz_grid_n<96>(int, cudaError_t*);
-template int x_pencils_n<96>();
 template size_t x_smem_n<96>(int, int, int);
 }  // namespace ys

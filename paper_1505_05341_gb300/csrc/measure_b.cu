@@ -3,10 +3,8 @@
 namespace ys {
 template cudaError_t run_measure_n<128>(Plan* const*, int, double* const*);
 template int yz_grid_n<128>(int, cudaError_t*);
-template int x_pencils_n<128>();
 template size_t x_smem_n<128>(int, int, int);
 template cudaError_t run_measure_n<192>(Plan* const*, int, double* const*);
 template int yz_grid_n<192>(int, cudaError_t*);
-template int x_pencils_n<192>();
 template size_t x_smem_n<192>(int, int, int);
 }  // namespace ys

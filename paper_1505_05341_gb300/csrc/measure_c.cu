@@ -3,10 +3,8 @@
 namespace ys {
 template cudaError_t run_measure_n<256>(Plan* const*, int, double* const*);
 template int yz_grid_n<256>(int, cudaError_t*);
-template int x_pencils_n<256>();
 template size_t x_smem_n<256>(int, int, int);
 template cudaError_t run_measure_n<384>(Plan* const*, int, double* const*);
 template int yz_grid_n<384>(int, cudaError_t*);
-template int x_pencils_n<384>();
 template size_t x_smem_n<384>(int, int, int);
 }  // namespace ys

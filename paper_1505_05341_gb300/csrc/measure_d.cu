@@ -3,6 +3,5 @@
 namespace ys {
 template cudaError_t run_measure_n<512>(Plan* const*, int, double* const*);
 template int yz_grid_n<512>(int, cudaError_t*);
-template int x_pencils_n<512>();
 template size_t x_smem_n<512>(int, int, int);
 }  // namespace ys

@@ -82,9 +82,9 @@ cudaError_t run_yz(Plan* const* lanes, int W) {
   return cudaGetLastError();
 }
 
-template <int N, int ELL, int M>
-cudaError_t run_x(Plan* const* lanes, int W) {
-  using XC = XCombine<N, ELL, M>;
+template <int N, int ELL, int M, int PX>
+cudaError_t run_x_p(Plan* const* lanes, int W) {
+  using XC = XCombine<N, ELL, M, PX>;
   Plan& p = *lanes[0];
   const int nbins = p.cfg.n_bins;
   cudaError_t err;
@@ -99,8 +99,8 @@ cudaError_t run_x(Plan* const* lanes, int W) {
       *per = 0;
       return cudaSuccess;
     }
-    cudaError_t e = cudaFuncSetAttribute(k_x_combine<N, ELL, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_x_combine<N, ELL, M>, XC::THREADS, sm);
+    cudaError_t e = cudaFuncSetAttribute(k_x_combine<N, ELL, M, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_x_combine<N, ELL, M, PX>, XC::THREADS, sm);
     return e;
   };
   int nwb = 1, per = 0, per_warp = 0;
@@ -121,7 +121,7 @@ cudaError_t run_x(Plan* const* lanes, int W) {
   }
   const size_t smem = XC::smem(nbins, nwb);
   if (smem > (size_t)smem_max) return cudaErrorInvalidConfiguration;
-  if ((err = cudaFuncSetAttribute(k_x_combine<N, ELL, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  if ((err = cudaFuncSetAttribute(k_x_combine<N, ELL, M, PX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return err;
   int dev = 0, sms = 0;
   if ((err = cudaGetDevice(&dev))) return err;
@@ -138,14 +138,17 @@ cudaError_t run_x(Plan* const* lanes, int W) {
   const int resident = std::max(1, per) * sms;
   const int grid = std::max(1, std::min(npb, (resident + W - 1) / W));
   LaunchScope ls(p, 6);
-  k_x_combine<N, ELL, M><<<dim3(grid, W), XC::THREADS, smem, p.stream>>>(pm, p.np_pad, p.d_pencil, p.d_tw, p.d_invw,
+  k_x_combine<N, ELL, M, PX><<<dim3(grid, W), XC::THREADS, smem, p.stream>>>(pm, p.np_pad, p.d_pencil, p.d_tw, p.d_invw,
                                                                          p.d_phase, p.d_lut, p.n2_hi, nbins, nwb);
   return cudaGetLastError();
 }
 
-// Pencils per x-stage CTA for mesh size N (for the host-side padding).
-template <int N>
-int x_pencils_n() { return k3_pencils(N); }
+// The x stage with the plan's current pencils per CTA.
+template <int N, int ELL, int M>
+cudaError_t run_x(Plan* const* lanes, int W) {
+  if (lanes[0]->x_pencils == k3_pencils_alt(N)) return run_x_p<N, ELL, M, k3_pencils_alt(N)>(lanes, W);
+  return run_x_p<N, ELL, M, k3_pencils(N)>(lanes, W);
+}
 
 // Dynamic shared memory of the x stage for mesh size N (independent of interlacing),
 // with nwb copies of the float shell bins.

@@ -398,8 +398,6 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid
   }
 }
 
-// Pencils per CTA of k_x_combine.
-__host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 512 ? 4 : 8); }
 
 // The x stage of several lanes (catalogues of one configuration, as for k_yz) in one
 // launch: grid (blocks per lane, lanes); the tables (pencils, twiddles, window, phases,
@@ -494,9 +492,9 @@ __device__ __forceinline__ float two_sum_err(float a, float b) {
   return (a - (s - bb)) + (b - bb);
 }
 
-template <int N, int ELL, int M>
+template <int N, int ELL, int M, int PX = k3_pencils(N)>
 struct XCombine {
-  static constexpr int P = k3_pencils(N);
+  static constexpr int P = PX;  // pencils per CTA
   static constexpr int E = fft_elems_lf(N);
   static constexpr int TPL = N / E;
   static constexpr int THREADS = P * TPL;
@@ -510,8 +508,8 @@ struct XCombine {
   static_assert(BOXES * BOX_ROWS == N, "boxes must tile the x axis");
   static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
-  // resident CTAs per SM the register budget is set for (3 x 256 threads from 256^3 up)
-  static constexpr int MIN_BLOCKS = ((N == 256 || N == 512) && ELL <= 4) ? 3 : 1;
+  // resident CTAs per SM the register budget is set for (3 x 256 threads at 256^3, 512^3)
+  static constexpr int MIN_BLOCKS = ((N == 256 || N == 512) && ELL <= 4 && THREADS == 256) ? 3 : 1;
   static_assert(THREADS % 32 == 0, "threads");
   // nwb copies of the compensated float shell bins: a sum and an error term per shell
   // and slot.  With nwb = NW c (c copies per warp) lane l of warp w adds into copy
@@ -526,8 +524,8 @@ struct XCombine {
   }
 };
 
-template <int N, int ELL, int M>
-__global__ void __launch_bounds__(XCombine<N, ELL, M>::THREADS, XCombine<N, ELL, M>::MIN_BLOCKS)
+template <int N, int ELL, int M, int PX>
+__global__ void __launch_bounds__(XCombine<N, ELL, M, PX>::THREADS, XCombine<N, ELL, M, PX>::MIN_BLOCKS)
 k_x_combine(const __grid_constant__ XMulti pm, int np_pad, const short2* __restrict__ pencil,
             const float2* __restrict__ tw_g, const float* __restrict__ invw_g, const float2* __restrict__ phase_g,
             const short* __restrict__ lut, int n2_hi, int nbins, int nwb) {
@@ -535,7 +533,7 @@ k_x_combine(const __grid_constant__ XMulti pm, int np_pad, const short2* __restr
   const CUtensorMap* gmap = &pm.map[blockIdx.y];
   double* __restrict__ acc = pm.acc[blockIdx.y];
   int* __restrict__ err = pm.err[blockIdx.y];
-  using XC = XCombine<N, ELL, M>;
+  using XC = XCombine<N, ELL, M, PX>;
   constexpr int P = XC::P, E = XC::E, TPL = XC::TPL, TILES = XC::TILES, RL = XC::RL;
   constexpr bool HORNER = x_horner<N, ELL>();
   constexpr int NBL = E / RL;

@@ -1,5 +1,6 @@
-// Autotuner: picks, by timing on the caller's catalogue, the scatter tile shape and
-// the grid of the persistent y,z kernel for one plan.  Not part of the method
+// Autotuner: picks, by timing on the caller's catalogue, the scatter tile shape (or
+// the direct assignment), the grid and ring lead of the persistent y,z kernel and
+// the x stage's FFT tile for one plan.  Not part of the method
 // (the paper runs on CPUs); it only chooses among configurations that compute the
 // same result.
 #include <cuda_runtime.h>
@@ -118,6 +119,27 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
     }
   }
   set_yz_grid(p, best_grid, best_pct);
+  // 4. the x stage's FFT tile (pencils per CTA): the default and its alternative; a
+  // tile the device cannot run (shared memory) is skipped
+  int best_px = p.x_pencils;
+  for (int px : {k3_pencils(p.n), k3_pencils_alt(p.n)}) {
+    if (px == best_px) continue;
+    if (set_x_pencils(p, px) != YS_OK) continue;
+    float ms = 0.f;
+    e = time_ms(p, reps, [&] { return launch_measure(p); }, &ms);
+    if (e) {
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best_measure) {
+      best_measure = ms;
+      best_px = px;
+    }
+  }
+  if (set_x_pencils(p, best_px) != YS_OK) {
+    why = "could not restore the x-stage tile";
+    return YS_ERR_CUDA;
+  }
   // the captured measurement graph holds the old launch shapes
   if (p.measure_exec) {
     cudaGraphExecDestroy(p.measure_exec);
@@ -133,6 +155,7 @@ ys_status autotune(Plan& p, const ys_catalog& gal, const ys_catalog& ran, int re
     out->ring_lead = p.ring_lead;
     out->assign_ms = best_assign;
     out->measure_ms = best_measure;
+    out->x_pencils = p.x_pencils;
   }
   return YS_OK;
 }

@@ -30,6 +30,14 @@ constexpr int TILE_X = 16, TILE_Y = 16, TILE_Z = 32;
 
 // Most catalogues of one configuration measured in one set of spectral launches.
 constexpr int YZ_MAX_LANES = 8;
+
+// Pencils per CTA of the x stage (its FFT tile): the default for mesh size n and the
+// alternative the autotuner also times.  Both are powers of two; the plan pads its
+// pencil list to a multiple of the larger.
+__host__ __device__ constexpr int k3_pencils(int n) { return n <= 32 ? 32 : (n >= 512 ? 4 : 8); }
+__host__ __device__ constexpr int k3_pencils_alt(int n) {
+  return n <= 32 ? 16 : (n >= 1024 ? 2 : (n >= 512 ? 8 : 4));
+}
 constexpr int kTileCandidates[5][3] = {{16, 16, 32}, {8, 16, 32}, {16, 16, 16}, {32, 16, 32}, {8, 8, 32}};
 
 struct Geom {
@@ -51,7 +59,8 @@ struct Plan {
   int ntiles = 0;
   // pencils (k_y, k_z) kept for the x transform: k_y^2 + k_z^2 < n2_hi
   int n2_hi = 0, nzc = 0, np = 0;
-  int np_pad = 0;                // np rounded up to whole x-stage pencil blocks
+  int np_pad = 0;                // np rounded up to whole x-stage pencil blocks (of either size)
+  int x_pencils = 0;             // pencils per x-stage CTA in use (k3_pencils or k3_pencils_alt)
   int ring_slots = 1;            // S: planes held by the y,z-stage ring
   int ring_lead = 1;             // D: column items trail row items by D planes
   int ring_lead_pct = 100;       // D relative to the work-balanced estimate (tuned)
@@ -134,6 +143,9 @@ cudaError_t launch_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran,
 cudaError_t launch_random_sums(Plan& p, const ys_catalog& ran, double* out);
 // Scatter tile shape (nodes per axis, capped at N); updates geom and ntiles.
 void set_tiles(Plan& p, int tx, int ty, int tz);
+// Pencils per x-stage CTA (k3_pencils or k3_pencils_alt of N): re-encodes the tensor
+// map of the grouped transforms for that box and drops the captured graph.
+ys_status set_x_pencils(Plan& p, int pencils);
 // y,z grid size; updates the ring lead D and slots S (S never exceeds the allocation).
 void set_yz_grid(Plan& p, int grid, int lead_pct = 0);
 constexpr int kRingLeadPctMax = 200;

@@ -78,7 +78,7 @@ class YsStats(ctypes.Structure):
 class YsTuning(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32 * 3), ("yz_grid", ctypes.c_int32), ("ring_lead", ctypes.c_int32),
                 ("assign_ms", ctypes.c_double),
-                ("measure_ms", ctypes.c_double)]
+                ("measure_ms", ctypes.c_double), ("x_pencils", ctypes.c_int32)]
 
 
 class YstatError(RuntimeError):
