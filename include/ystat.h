@@ -145,6 +145,19 @@ ys_status ys_randoms_cache(ys_plan* plan, const ys_catalog* ran);
  * rounding.  YS_ERR_STATE without a ys_randoms_cache.  Asynchronous. */
 ys_status ys_assign_cached(ys_plan* plan, const ys_catalog* gal);
 
+/* The assigned mesh F of Eq. (1), as the transforms read it: m meshes of n_mesh^3
+ * floats (m = 2 when interlaced; the second has its nodes at +H/2 on every axis),
+ * each x-major with z fastest.  Copies the m n_mesh^3 floats to dst, a DEVICE or HOST
+ * pointer owned by the caller, on the plan's stream and waits for the copy.  With
+ * the sorted assignment each node is summed exactly in fixed point (every stencil
+ * weight rounded to 2^-s, s set per tile from its largest |w| and its record count,
+ * far below float resolution), so the mesh does not depend on the order of the
+ * particles; tiles with a non-finite weight, tile shapes that do not fit twice in
+ * shared memory, and the direct assignment sum in float.
+ * YS_ERR_ARG for a null pointer or count < m n_mesh^3, YS_ERR_STATE before an
+ * assignment. */
+ys_status ys_plan_copy_mesh(ys_plan* plan, float* dst, int64_t count);
+
 /* Eqs. (4)-(13): the LOS-weighted fields, their FFTs, the k-space combination,
  * the shell sums and Eqs. (6)-(8).  Writes the device result row
  *   d_out[0 .. 5 n_bins + 5) = [k_mean | n_modes | p0 | p2 | p4 |
@@ -265,7 +278,7 @@ ys_status ys_plan_set_fault_injection(ys_plan* plan, int64_t wait_limit_ns, int3
  * and catalogue sums, consumed by the next ys_measure_multipoles*.  Asynchronous on
  * the plan's stream.
  * Limits: the records need (gal->n + ran->n) * T * 16 bytes, T = 2^(axes with more
- * than one tile in the plan's current scatter-tile shape) <= 8 -- 16 x 16 x 32 nodes
+ * than one tile in the plan's current scatter-tile shape) <= 8 -- 16 x 16 x 16 nodes
  * unless ys_plan_autotune picked another shape -- plus 12 bytes per tile; a catalogue
  * that does not fit returns YS_ERR_UNSUPPORTED before any work is queued
  * (ys_last_cuda_error() then gives the sizes).  For a 256^3 mesh (T = 8) this is

@@ -826,6 +826,17 @@ ys_status ys_plan_set_direct_assign(ys_plan* plan, int enable) {
   return YS_OK;
 }
 
+ys_status ys_plan_copy_mesh(ys_plan* plan, float* dst, int64_t count) {
+  if (!plan || !dst) return YS_ERR_ARG;
+  Plan& p = plan->p;
+  const int64_t total = (int64_t)p.m * p.n * p.n * p.n;
+  if (count < total) return YS_ERR_ARG;
+  if (!p.assigned) return YS_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(dst, p.d_mesh, sizeof(float) * (size_t)total, cudaMemcpyDefault, p.stream);
+  if (!e) e = cudaStreamSynchronize(p.stream);
+  return e ? ys::cuda_fail(e) : YS_OK;
+}
+
 ys_status ys_plan_set_profiling(ys_plan* plan, int enable) {
   if (!plan) return YS_ERR_ARG;
   plan->p.profiling = enable != 0;

@@ -4,16 +4,19 @@
 //
 // GB300 design: particles arrive in random order, and a direct global atomic
 // deposit onto a 0.5-1 GB mesh would miss L2 on almost every update.  Instead a
-// counting sort groups particles by mesh tile (16 x 16 x 32 nodes, both meshes of an
-// interlaced pair held together), and one CTA per tile accumulates its nodes in
-// shared memory with shared-memory atomics, then writes the tile with coalesced
-// plain stores.  A particle whose stencil crosses tile borders is listed once per
+// counting sort groups particles by mesh tile (16 x 16 x 16 nodes by default, both
+// meshes of an interlaced pair held together), and one CTA per tile accumulates its
+// nodes in shared memory with integer shared-memory atomics (exact fixed-point sums),
+// then writes the tile with coalesced plain stores.  A particle whose stencil crosses tile borders is listed once per
 // tile it touches (at most 8), so tiles never write each other's nodes: no global
 // atomics on the mesh and no zero-fill pass.
 //
 //   k_count   : cell index per particle, FP64-accumulated sums, per-tile counts
 //   k_scan    : exclusive scan of the counts (one CTA)
-//   k_bin     : one 16-byte record (position, signed weight) per tile touched
+//   k_bin     : one 16-byte record (position, signed weight) per tile touched;
+//               records whose stencils lie inside one tile fill its list from the
+//               front, the others from the back, so the deposit walks the interior
+//               ones without per-node range checks
 //               (the deposit locates the particle again: 20-byte records with the
 //               cell index cost two partial L2 sector writes each)
 //   k_deposit : per-tile shared-memory deposit and store
@@ -167,11 +170,13 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
     ok &= locate(y, 1, g, nodes, ci[1], cd[1]);
     ok &= locate(z, 2, g, nodes, ci[2], cd[2]);
     int tt[3][2], nt[3];
+    bool inner = true;  // every stencil node in one tile, no periodic wrap
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       int lo, hi;
       node_range<KIND, M>(ci[a], cd[a], lo, hi);
       nt[a] = axis_tiles(lo, hi, g.n, g.tdim[a], tt[a]);
+      inner &= nt[a] == 1 && lo >= 0 && hi < g.n;
     }
     if (!BIN) {
       bad += ok ? 0u : 1u;
@@ -195,7 +200,9 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
             if (HIST) atomicAdd(&s_hist[tile], 1u);
             else atomicAdd(&tile_count[tile], 1u);
           } else {
-            const unsigned slot = atomicAdd(&tile_cur[tile], 1u);
+            // interior records fill the tile's list from the front, the others
+            // from the back (tile_count holds the end of each list after the scan)
+            const unsigned slot = inner ? atomicAdd(&tile_cur[tile], 1u) : atomicSub(&tile_count[tile], 1u) - 1u;
             rec[slot] = make_float4(x, y, z, weff);
           }
         }
@@ -230,9 +237,10 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
   }
 }
 
-// Exclusive scan of the tile counts (single CTA of 1024 threads).
+// Exclusive scan of the tile counts (single CTA of 1024 threads); the counts are
+// replaced by the end of each tile's list, the binning pass's back cursors.
 __global__ void __launch_bounds__(1024)
-k_scan(const unsigned* __restrict__ count, int ntiles, unsigned* __restrict__ off, unsigned* __restrict__ cur) {
+k_scan(unsigned* __restrict__ count, int ntiles, unsigned* __restrict__ off, unsigned* __restrict__ cur) {
   __shared__ unsigned part[1024];
   const int t = threadIdx.x;
   const int per = (ntiles + 1023) / 1024;
@@ -252,18 +260,121 @@ k_scan(const unsigned* __restrict__ count, int ntiles, unsigned* __restrict__ of
     off[i] = run;
     cur[i] = run;
     run += count[i];
+    count[i] = run;  // from here on the back cursor of tile i
   }
   if (t == 1023) off[ntiles] = part[1023];
 }
 
+// Stencil walk of one record: add(k, wxy, wz) for every node of the record's stencil,
+// k the node's index in the tile's (mesh, x, y, z) order and its weight the product
+// wxy * wz (wxy = wq W_x W_y, wz = W_z).  A node outside this tile goes to `trash`
+// (a per-lane word past the tile that is never read): in a warp of 32 records nearly
+// every stencil node is inside for some lane, so branching per node saves no adds
+// and costs a divergent branch each.
+template <int KIND, int M, class Add>
+__device__ __forceinline__ void deposit_record(const float4& q, float wq, const Geom& g,
+                                               const float2* __restrict__ nodes, const int (&o)[3],
+                                               const int (&td)[3], int tvol, int trash, Add&& add) {
+  const int n = g.n;
+  int ci[3];
+  float cd[3];  // the cell and offset the binning pass found (same arithmetic)
+  locate(q.x, 0, g, nodes, ci[0], cd[0]);
+  locate(q.y, 1, g, nodes, ci[1], cd[1]);
+  locate(q.z, 2, g, nodes, ci[2], cd[2]);
+#pragma unroll
+  for (int mj = 0; mj < M; ++mj) {
+    int loc[3][3];
+    float wt[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int first;
+      stencil<KIND>(ci[a], cd[a], mj == 1, first, wt[a]);
+#pragma unroll
+      for (int s = 0; s < KIND; ++s) {
+        const int l = wrapn(first + s - o[a], n);  // first + s in [-1, n + 1]; o[a] in [0, n)
+        loc[a][s] = (l >= 0 && l < td[a]) ? l : -1;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < KIND; ++a) {
+#pragma unroll
+      for (int bb = 0; bb < KIND; ++bb) {
+        const float wxy = wq * wt[0][a] * wt[1][bb];
+        const bool in_row = loc[0][a] >= 0 && loc[1][bb] >= 0;
+        const int row = mj * tvol + (loc[0][a] * td[1] + loc[1][bb]) * td[2];
+#pragma unroll
+        for (int c = 0; c < KIND; ++c) add(in_row && loc[2][c] >= 0 ? row + loc[2][c] : trash, wxy, wt[2][c]);
+      }
+    }
+  }
+}
+
+// Stencil walk of an interior record (every node of both stencils inside this tile,
+// no periodic wrap): the same weights and node order as deposit_record, without the
+// per-node range checks, and with the nodes of one (x, y) row at fixed offsets.
+template <int KIND, int M, class Add>
+__device__ __forceinline__ void deposit_inner(const float4& q, float wq, const Geom& g,
+                                              const float2* __restrict__ nodes, const int (&o)[3],
+                                              const int (&td)[3], int tvol, Add&& add) {
+  int ci[3];
+  float cd[3];
+  locate(q.x, 0, g, nodes, ci[0], cd[0]);
+  locate(q.y, 1, g, nodes, ci[1], cd[1]);
+  locate(q.z, 2, g, nodes, ci[2], cd[2]);
+#pragma unroll
+  for (int mj = 0; mj < M; ++mj) {
+    int first[3];
+    float wt[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) stencil<KIND>(ci[a], cd[a], mj == 1, first[a], wt[a]);
+    const int base = mj * tvol + ((first[0] - o[0]) * td[1] + (first[1] - o[1])) * td[2] + (first[2] - o[2]);
+#pragma unroll
+    for (int a = 0; a < KIND; ++a)
+#pragma unroll
+      for (int bb = 0; bb < KIND; ++bb) {
+        const float wxy = wq * wt[0][a] * wt[1][bb];
+        const int row = base + (a * td[1] + bb) * td[2];
+#pragma unroll
+        for (int c = 0; c < KIND; ++c) add(row + c, wxy, wt[2][c]);
+      }
+  }
+}
+
+// Per-tile deposit.  FIXED (the tile fits twice in shared memory): the node sums are
+// kept in fixed point, as two int32 words per node, because shared-memory integer
+// atomics are several times faster than float ones and integer sums are exact.
+//
+// Fixed point.  A node value v is stored as V = v 2^s (units of 2^-s), split into
+// hi 2^sb + lo with |lo| <= 2^(sb-1); hi and lo are summed in separate int32 arrays.
+// With n < 2^30 records in the tile and w_m the largest |w| among them:
+//   sb = min(22, floor(31 - log2 n))  => n 2^(sb-1) <= 2^30: the lo sums cannot
+//                                        overflow;
+//   s  = floor(min(30 + sb - log2(n w_m), 21 + sb - log2 w_m))
+//      => |V| <= 2^(21+sb) for one stencil weight (|W| <= 1), which the rounding
+//         below needs, and sum |V| <= 2^(30+sb), so the hi sums stay below
+//         2^30 + n/2 < 2^31.  (A float log2 off in its last bits moves these bounds by
+//         a factor 1 + 1e-6, well inside the slack.)
+// One stencil weight V = wxy wz 2^s (wxy already carries 2^s, an exact power-of-two
+// scaling) is split without conversion instructions: fma(wxy, wz, K) with
+// K = 1.5 2^(23+sb) rounds V to a multiple of 2^sb, and the bit pattern of the
+// result minus that of K is V / 2^sb rounded (hi); fma(wxy, wz, -(t - K)) is the
+// remainder to one float rounding, and adding 1.5 2^23 rounds it to an integer (lo).
+// Each stencil weight is thus quantised to 2^-s (2^-37 of the largest weight for a
+// tile of ~3000 records; 2^-17 of it for one of a million, still far finer than
+// float sums, which drop every weight below half an ulp of a large node) and the sums
+// are exact, so the mesh is the same bit for bit whatever order the records arrive
+// in.  A tile with a non-finite weight (or 2^30 or more records) is summed in float
+// instead, so that a NaN reaches exactly the nodes it touches.
+//
 // rmesh (shared randoms): the kept random mesh sum_ran w W, written as
 // F = (galaxy deposit) - alpha rmesh, with alpha from the catalogue sums.
-template <int KIND, int M>
-__global__ void __launch_bounds__(THREADS)
+template <int KIND, int M, bool FIXED>
+__global__ void __launch_bounds__(THREADS, 3)
 k_deposit(Geom g, const float2* __restrict__ nodes, const unsigned* __restrict__ off,
-          const float4* __restrict__ rec, float* __restrict__ mesh, const float* __restrict__ rmesh,
-          const double* __restrict__ sums, double alpha_cfg) {
+          const unsigned* __restrict__ split, const float4* __restrict__ rec, float* __restrict__ mesh,
+          const float* __restrict__ rmesh, const double* __restrict__ sums, double alpha_cfg) {
   extern __shared__ float s_tile[];
+  __shared__ float s_wmax[THREADS / 32];
   const int n = g.n;
   const int tdx = g.tdim[0], tdy = g.tdim[1], tdz = g.tdim[2];
   const int tvol = tdx * tdy * tdz;
@@ -273,60 +384,94 @@ k_deposit(Geom g, const float2* __restrict__ nodes, const unsigned* __restrict__
   const int tx = tile / (g.tiles[2] * g.tiles[1]);
   const int o[3] = {tx * tdx, ty * tdy, tz * tdz};
   const int td[3] = {tdx, tdy, tdz};
-  for (int k = threadIdx.x; k < M * tvol; k += blockDim.x) s_tile[k] = 0.f;
-  __syncthreads();
   const unsigned b = off[tile], e = off[tile + 1];
-  for (unsigned r = b + threadIdx.x; r < e; r += blockDim.x) {
-    const float4 q = rec[r];
-    int ci[3];
-    float cd[3];  // the cell and offset the binning pass found (same arithmetic)
-    locate(q.x, 0, g, nodes, ci[0], cd[0]);
-    locate(q.y, 1, g, nodes, ci[1], cd[1]);
-    locate(q.z, 2, g, nodes, ci[2], cd[2]);
+  const unsigned mid = split[tile];  // records [b, mid) are interior, [mid, e) cross a border
+  const unsigned nrec = e - b;
+  bool fixed = false;
+  int sb = 0, sc = 0;  // split bits and scale exponent s
+  // Layout: M tvol node words + 32 trash words, twice when FIXED (hi, then lo).
+  const int words = M * tvol + 32;
+  const int trash = M * tvol + (threadIdx.x & 31);
+  if (FIXED) {
+    for (int k = threadIdx.x; k < 2 * words; k += blockDim.x) s_tile[k] = 0.f;
+    const float* wrec = reinterpret_cast<const float*>(rec) + 3;
+    float wm = 0.f;
+    bool bad = false;
+    for (unsigned r = b + threadIdx.x; r < e; r += blockDim.x) {
+      const float w = wrec[(size_t)r * 4];
+      bad |= !isfinite(w);
+      wm = fmaxf(wm, fabsf(w));
+    }
 #pragma unroll
-    for (int mj = 0; mj < M; ++mj) {
-      int loc[3][3];
-      float wt[3][3];
+    for (int k = 16; k > 0; k >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, k));
+    if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = wm;
+    bad = __syncthreads_or(bad);  // also orders s_wmax and the zero fill
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int first;
-        stencil<KIND>(ci[a], cd[a], mj == 1, first, wt[a]);
-#pragma unroll
-        for (int s = 0; s < KIND; ++s) {
-          const int l = wrapn(first + s - o[a], n);  // first + s in [-1, n + 1]; o[a] in [0, n)
-          loc[a][s] = (l >= 0 && l < td[a]) ? l : -1;
-        }
-      }
-      float* st = s_tile + mj * tvol;
-#pragma unroll
-      for (int a = 0; a < KIND; ++a) {
-        if (loc[0][a] < 0) continue;
-#pragma unroll
-        for (int bb = 0; bb < KIND; ++bb) {
-          if (loc[1][bb] < 0) continue;
-          const float wxy = q.w * wt[0][a] * wt[1][bb];
-          float* row = st + (loc[0][a] * tdy + loc[1][bb]) * tdz;
-#pragma unroll
-          for (int c = 0; c < KIND; ++c) {
-            if (loc[2][c] < 0) continue;
-            atomicAdd(row + loc[2][c], wxy * wt[2][c]);
-          }
-        }
-      }
+    for (int k = 0; k < THREADS / 32; ++k) wm = fmaxf(wm, s_wmax[k]);
+    fixed = !bad && nrec < (1u << 30);
+    if (fixed && nrec > 0) {
+      const float ln = log2f((float)nrec), lw = log2f(wm);
+      sb = min(22, (int)floorf(31.f - ln));
+      // s <= 100 only loses resolution; weights beyond ~2^100 (s < -100) sum in float
+      const float sf = wm > 0.f ? floorf(fminf(30.f + sb - ln - lw, 21.f + sb - lw)) : 0.f;
+      fixed = sf >= -100.f;
+      sc = (int)fminf(100.f, fmaxf(sf, -100.f));
+    }
+  } else {
+    for (int k = threadIdx.x; k < M * tvol; k += blockDim.x) s_tile[k] = 0.f;
+    __syncthreads();
+  }
+  if (fixed) {
+    int* s_hi = reinterpret_cast<int*>(s_tile);
+    int* s_lo = s_hi + words;
+    const float scale = __int_as_float((127 + sc) << 23);            // 2^s
+    const int kbits = ((127 + 23 + sb) << 23) | 0x400000;            // 1.5 2^(23+sb)
+    const float kh = __int_as_float(kbits);
+    auto add = [&](int k, float wxy, float wz) {
+      const float t = __fmaf_rn(wxy, wz, kh);
+      const float lf = __fmaf_rn(wxy, wz, -__fsub_rn(t, kh));
+      atomicAdd(s_hi + k, __float_as_int(t) - kbits);
+      atomicAdd(s_lo + k, __float_as_int(__fadd_rn(lf, 12582912.f)) - 0x4B400000);  // + 1.5 2^23
+    };
+    for (unsigned r = b + threadIdx.x; r < mid; r += blockDim.x) {
+      const float4 q = rec[r];
+      deposit_inner<KIND, M>(q, q.w * scale, g, nodes, o, td, tvol, add);
+    }
+    for (unsigned r = mid + threadIdx.x; r < e; r += blockDim.x) {
+      const float4 q = rec[r];
+      deposit_record<KIND, M>(q, q.w * scale, g, nodes, o, td, tvol, trash, add);
+    }
+  } else {
+    auto add = [&](int k, float wxy, float wz) { atomicAdd(s_tile + k, wxy * wz); };
+    for (unsigned r = b + threadIdx.x; r < mid; r += blockDim.x) {
+      const float4 q = rec[r];
+      deposit_inner<KIND, M>(q, q.w, g, nodes, o, td, tvol, add);
+    }
+    for (unsigned r = mid + threadIdx.x; r < e; r += blockDim.x) {
+      const float4 q = rec[r];
+      deposit_record<KIND, M>(q, q.w, g, nodes, o, td, tvol, trash, add);
     }
   }
   __syncthreads();
   const size_t n3 = (size_t)n * n * n;
   const float ran_scale =
       rmesh ? (float)(-(alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR])) : 0.f;
+  // hi 2^sb + lo in units of 2^-s, in float: each int32 rounds to float once and the
+  // fma once more (within one ulp of the exact sum, and the same bits on every run)
+  const float unscale = __int_as_float((127 - sc) << 23);       // 2^-s
+  const float hscale = __int_as_float((127 + sb - sc) << 23);   // 2^(sb-s)
+  const int* s_hi = reinterpret_cast<const int*>(s_tile);
+  // tile sides are powers of two (8, 16 or 32 for every supported mesh)
+  const int shz = __ffs(tdz) - 1, shy = __ffs(tdy) - 1, shv = shz + shy + __ffs(tdx) - 1;
   for (int k = threadIdx.x; k < M * tvol; k += blockDim.x) {
-    const int mj = k / tvol;
-    const int rr = k - mj * tvol;
-    const int lz = rr % tdz;
-    const int ly = (rr / tdz) % tdy;
-    const int lx = rr / (tdz * tdy);
+    const int mj = k >> shv;
+    const int lz = k & (tdz - 1);
+    const int ly = (k >> shz) & (tdy - 1);
+    const int lx = (k >> (shz + shy)) & (tdx - 1);
     const size_t at = mj * n3 + ((size_t)(o[0] + lx) * n + (o[1] + ly)) * n + (o[2] + lz);
-    mesh[at] = rmesh ? fmaf(ran_scale, rmesh[at], s_tile[k]) : s_tile[k];
+    const float v = fixed ? __fmaf_rn(__int2float_rn(s_hi[k]), hscale, __int2float_rn(s_hi[words + k]) * unscale)
+                          : s_tile[k];
+    mesh[at] = rmesh ? fmaf(ran_scale, rmesh[at], v) : v;
   }
 }
 
@@ -528,18 +673,26 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, co
     if (k.n == 0) continue;
     LaunchScope ls(p, 2);
     k_particles<KIND, M, true><<<blocks(k.n), THREADS, 0, st>>>(
-        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, nullptr, p.d_tile_cur, p.d_rec,
+        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, p.d_tile_cur, p.d_rec,
         p.d_sums, p.cfg.alpha, p.ntiles);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int tvol = p.geom.tdim[0] * p.geom.tdim[1] * p.geom.tdim[2];
-  const size_t smem = sizeof(float) * M * tvol;
-  if ((err = cudaFuncSetAttribute(k_deposit<KIND, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
+  int dev = 0, optin = 0;
+  if ((err = cudaGetDevice(&dev)) ||
+      (err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)))
+    return err;
+  // fixed-point sums need two words per node; a tile that cannot hold them sums in float
+  const size_t words = (size_t)M * tvol + 32;  // nodes and one trash word per lane
+  const size_t smem_fixed = 2 * sizeof(float) * words;
+  const bool fixed = smem_fixed + 64 <= (size_t)optin;
+  const size_t smem = fixed ? smem_fixed : sizeof(float) * words;
+  auto kern = fixed ? k_deposit<KIND, M, true> : k_deposit<KIND, M, false>;
+  if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return err;
   LaunchScope ls(p, 3);
-  k_deposit<KIND, M><<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_nodes, p.d_tile_off, p.d_rec, p.d_mesh, rmesh,
-                                                       p.d_sums, p.cfg.alpha);
+  kern<<<p.ntiles, THREADS, smem, st>>>(p.geom, p.d_nodes, p.d_tile_off, p.d_tile_cur, p.d_rec, p.d_mesh, rmesh,
+                                        p.d_sums, p.cfg.alpha);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ enum SumSlot {
 // Tile of the scatter: TX x TY x TZ mesh nodes per CTA (capped at N per axis); the
 // default and the shapes the autotuner tries (each divides every supported N once
 // capped; shared memory = meshes x nodes x 4 bytes).
-constexpr int TILE_X = 16, TILE_Y = 16, TILE_Z = 32;
+constexpr int TILE_X = 16, TILE_Y = 16, TILE_Z = 16;
 
 // Most catalogues of one configuration measured in one set of spectral launches.
 constexpr int YZ_MAX_LANES = 8;

@@ -116,6 +116,7 @@ def _lib():
         lib.ys_plan_set_profiling.argtypes = [P, ctypes.c_int]
         lib.ys_plan_set_fault_injection.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
         lib.ys_plan_set_direct_assign.argtypes = [P, ctypes.c_int]
+        lib.ys_plan_copy_mesh.argtypes = [P, P, ctypes.c_int64]
         lib.ys_plan_get_stats.argtypes = [P, ctypes.POINTER(YsStats), ctypes.c_int]
         lib.ys_plan_autotune.argtypes = [P, ctypes.POINTER(YsCatalog), ctypes.POINTER(YsCatalog), ctypes.c_int32,
                                          ctypes.POINTER(YsTuning)]
@@ -337,6 +338,15 @@ class Plan:
             return res
         w = wd.cpu().numpy()
         return res, (w[:self.n_bins], w[self.n_bins:])
+
+    def mesh(self):
+        """ys_plan_copy_mesh: the assigned mesh(es) as a host float32 array (m, n, n, n),
+        x-major with z fastest; m = 2 when interlaced."""
+        n = self.cfg.n_mesh
+        m = 2 if self.cfg.interlace else 1
+        out = np.empty((m, n, n, n), dtype=np.float32)
+        _check(_lib().ys_plan_copy_mesh(self._h, out.ctypes.data, out.size), "ys_plan_copy_mesh")
+        return out
 
     def set_fault_injection(self, wait_limit_ns=0, skip_plane=-1):
         """ys_plan_set_fault_injection: bound of the y,z-stage waits, and the plane whose
