@@ -108,7 +108,7 @@ cudaError_t run_x_p(Plan* const* lanes, int W) {
   if (per_warp > 0) {
     nwb = XC::NW;
     per = per_warp;
-    for (int c : {4, 2}) {
+    for (int c : {8, 4, 2}) {
       int pc = 0;
       if ((err = occupancy(XC::NW * c, &pc))) return err;
       if (pc >= per_warp) {

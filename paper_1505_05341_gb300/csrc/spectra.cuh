@@ -512,10 +512,11 @@ struct XCombine {
   static constexpr int MIN_BLOCKS = ((N == 256 || N == 512) && ELL <= 4 && THREADS == 256) ? 3 : 1;
   static_assert(THREADS % 32 == 0, "threads");
   // nwb copies of the compensated float shell bins: a sum and an error term per shell
-  // and slot.  With nwb = NW c (c copies per warp) lane l of warp w adds into copy
-  // w c + l mod c, which divides the lanes that hit one address in one instruction
-  // (same-address shared atomics are served one after another); with fewer copies
-  // warp w adds into copy w mod nwb.
+  // and slot.  With nwb = NW c (c copies per warp) lane l = p + P j of warp w adds into
+  // copy w c + j mod c, which divides the lanes of one pencil (neighbouring k_x, mostly
+  // one shell) that would hit one address in one instruction (same-address shared
+  // atomics are served one after another); with fewer copies warp w adds into copy
+  // w mod nwb.
   static size_t smem(int nbins, int nwb) {
     size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
@@ -674,38 +675,51 @@ k_x_combine(const __grid_constant__ XMulti pm, int np_pad, const short2* __restr
           ga[e] = make_float2(c * (ga[e].x + gl[e].x), c * (ga[e].y + gl[e].y));
         }
       }
-      const int copy = nwb >= XC::NW ? warp * (nwb / XC::NW) + (tid & 31) % (nwb / XC::NW) : warp % nwb;
+      // the lanes of one pencil (lane = p + P j) hold neighbouring k_x, mostly in one
+      // shell: spread them over the warp's copies by j
+      const int copy = nwb >= XC::NW ? warp * (nwb / XC::NW) + ((tid & 31) / P) % (nwb / XC::NW) : warp % nwb;
       float* wb = wbin + (copy * SLOTS + slot) * nbins;
       float* wc = wb + nwb * SLOTS * nbins;
       const float wgt = kz == 0 ? 1.f : 2.f;
-      // Half of the modes at a time: their sums first, so that the atomics' latencies
-      // overlap, then the rounding errors.
-      constexpr int EH = E / 2;
+      // The lanes of one pencil (lane = p + P j, j < 32 / P) hold neighbouring k_x and
+      // mostly share a shell: each run of equal shells (cut wherever neighbouring lanes
+      // differ) is first summed across its lanes by a segmented suffix scan with
+      // compensated adds, and only the run's first lane adds it to the bins.
+      const int lane = tid & 31, jl = lane / P;
+      constexpr int LG = 32 / P;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float val[EH], old[EH];
+      for (int e = 0; e < E; ++e) {
+        const int kx = tl + (e / RL) * TPL + (e % RL) * (N / RL);
+        const int mx = kx <= N / 2 ? kx : kx - N;
+        float val;
+        if (slot == 0) {
+          val = wgt * (a0[e].x * a0[e].x + a0[e].y * a0[e].y);
+        } else {
+          const float inv = 1.f / (float)(mx * mx + ky * ky + kz * kz);
+          const float ik = slot == 1 ? inv : (slot == 2 ? inv * inv : inv * inv * inv);  // 1 / k^(2 slot)
+          val = wgt * ik * (a0[e].x * ga[e].x + a0[e].y * ga[e].y);
+        }
+        const int key = bins[e];
+        const int key_next = __shfl_down_sync(0xffffffffu, key, P);
+        const int key_prev = __shfl_up_sync(0xffffffffu, key, P);
+        int end = (jl == LG - 1 || key_next != key) ? 1 : 0;  // this lane's run stops here
+        float cmp = 0.f;
 #pragma unroll
-        for (int i = 0; i < EH; ++i) {
-          const int e = h * EH + i;
-          const int kx = tl + (e / RL) * TPL + (e % RL) * (N / RL);
-          const int mx = kx <= N / 2 ? kx : kx - N;
-          if (slot == 0) {
-            val[i] = wgt * (a0[e].x * a0[e].x + a0[e].y * a0[e].y);
-          } else {
-            const float inv = 1.f / (float)(mx * mx + ky * ky + kz * kz);
-            const float ik = slot == 1 ? inv : (slot == 2 ? inv * inv : inv * inv * inv);  // 1 / k^(2 slot)
-            val[i] = wgt * ik * (a0[e].x * ga[e].x + a0[e].y * ga[e].y);
+        for (int d = P; d < 32; d <<= 1) {
+          const float vn = __shfl_down_sync(0xffffffffu, val, d);
+          const float cn = __shfl_down_sync(0xffffffffu, cmp, d);
+          const int en = __shfl_down_sync(0xffffffffu, end, d);
+          if (!end) {  // the run reaches lane + d, inside this pencil's lanes
+            cmp += cn + two_sum_err(val, vn);
+            val += vn;
+            end = en;
           }
         }
-#pragma unroll
-        for (int i = 0; i < EH; ++i)
-          if (bins[h * EH + i] >= 0) old[i] = atomicAdd(wb + bins[h * EH + i], val[i]);
-#pragma unroll
-        for (int i = 0; i < EH; ++i)
-          if (bins[h * EH + i] >= 0) {
-            const float err = two_sum_err(old[i], val[i]);
-            if (err != 0.f) atomicAdd(wc + bins[h * EH + i], err);
-          }
+        if (key >= 0 && (jl == 0 || key_prev != key)) {
+          const float old = atomicAdd(wb + key, val);
+          const float err = cmp + two_sum_err(old, val);
+          if (err != 0.f) atomicAdd(wc + key, err);
+        }
       }
     }
     __syncthreads();
