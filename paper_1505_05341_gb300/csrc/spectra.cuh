@@ -237,6 +237,14 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
   }
 }
 
+// 1/x for a normal x > 0: the hardware approximation refined by one Newton-Raphson
+// step, y' = y + y (1 - x y), which leaves it within about an ulp (the correctly
+// rounded reciprocal costs a long instruction sequence per node).
+__device__ __forceinline__ float recip_nr(float x) {
+  const float y = __fdividef(1.f, x);
+  return fmaf(y, fmaf(-x, y, 1.f), y);
+}
+
 // Row item: the mesh value F and 1/|r|^2 of every node of the R rows are formed once
 // (each thread for the nodes it later reads, so no barrier is needed), then every
 // pair of basis fields is built from them, transformed along z and split.
@@ -262,7 +270,7 @@ __device__ __forceinline__ void row_item(float2* work, float2* nodes, const floa
           const int z = fft_in_index<N>(tl, q, r);
           const float Zc = relz[z];
           const float r2 = fmaf(Zc, Zc, xy2);
-          nrow[z] = make_float2(frow[z], r2 > 0.f ? __frcp_rn(r2) : 0.f);
+          nrow[z] = make_float2(frow[z], r2 > 0.f ? recip_nr(r2) : 0.f);
         }
     }
   }
@@ -360,6 +368,21 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid
     __syncthreads();
     const int gitem = s_item;
     if (gitem >= total) break;
+    {  // L2 prefetch of the mesh rows of the row item one grid of tickets ahead
+      const int ahead = gitem + (int)gridDim.x;
+      if (ahead < total && threadIdx.x < R * N / 32) {
+        int la = 0;
+        while (ahead >= pm.end[la]) ++la;
+        const YZParams& pa = pm.lane[la];
+        const int ia = ahead - (la > 0 ? pm.end[la - 1] : 0);
+        const int ipa = NZ + pa.nzc, sta = ia / ipa, sba = ia - sta * ipa;
+        if (sba < NZ && sta < pa.m * N) {
+          const int ja = sta / N, xa = sta - ja * N;
+          const float* rows = pa.mesh + ja * n3 + (size_t)xa * N * N + (size_t)sba * R * N;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(rows + threadIdx.x * 32));  // one 128-byte line each
+        }
+      }
+    }
     int l = 0;
     while (gitem >= pm.end[l]) ++l;
     const YZParams& prm = pm.lane[l];
