@@ -43,26 +43,31 @@ namespace ys {
 // costs one reciprocal of |r|^2 shared by all fields plus two or three products per
 // field.
 
-// v^e for a small run-time exponent 0 <= e <= 7 (warp-uniform), by the bits of e.
-__device__ __forceinline__ float ipow_rt(float v, int e) {
+// v^EXP for a small exponent 0 <= EXP <= 7, by the bits of EXP.
+template <int EXP>
+__device__ __forceinline__ float ipow_ct(float v) {
   const float v2 = v * v;
-  float r = (e & 1) ? v : 1.f;
-  if (e & 2) r *= v2;
-  if (e & 4) r *= v2 * v2;
+  float r = (EXP & 1) ? v : 1.f;
+  if constexpr ((EXP & 2) != 0) r *= v2;
+  if constexpr ((EXP & 4) != 0) r *= v2 * v2;
   return r;
 }
 
 // Field value at a node: f the mesh value, i2 = 1/|r|^2 (0 where r = 0), z = Z, K the
-// line constant X^a Y^b; c, d warp-uniform (d = 2, 4 or 6 divides by |r|^d).
-__device__ __forceinline__ float basis_value_rt(float f, float i2, float z, float K, int c, int d) {
-  if (d == 0) return f;
-  if (d == -1) return i2 > 0.f ? f : 0.f;
-  if (d == -2) return 0.f;
-  float v = (f * K) * i2;
-  if (d >= 4) v *= i2;
-  if (d == 6) v *= i2;
-  if (c) v *= z;
-  return v;
+// line constant X^a Y^b; C, D the field's z power and degree (D = 2, 4 or 6 divides
+// by |r|^D).  Each pair of fields is built with its exponents known at compile time.
+template <int C, int D>
+__device__ __forceinline__ float basis_value_ct(float f, float i2, float z, float K) {
+  if constexpr (D == 0) return f;
+  else if constexpr (D == -1) return i2 > 0.f ? f : 0.f;
+  else if constexpr (D == -2) return 0.f;
+  else {
+    float v = (f * K) * i2;
+    if constexpr (D >= 4) v *= i2;
+    if constexpr (D == 6) v *= i2;
+    if constexpr (C != 0) v *= z;
+    return v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -167,21 +172,23 @@ struct YZ {
 };
 
 
-// One pair of basis fields (fa = 2 pr, fb = 2 pr + 1) for the R rows of a row item:
-// fields at the nodes (first FFT stage from registers, one butterfly at a time),
-// FFT along z, then the split of the two real fields into their half spectra,
-// written to the ring slot.  C is one of two line buffers, so the split of this pair
-// can overlap the FFT of the next.
-template <int N, int ELL>
-__device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes, float X,
-                                         const float* __restrict__ rely, const float* __restrict__ relz, int row0,
-                                         const float2* tw, float2* __restrict__ zslot, int nzc) {
+// Monomial of basis field beta (its exponents a, b, c and degree d, i = 0..3) at
+// compile time; fields past the last one (an odd count's partner) are zero.
+template <int ELL>
+__host__ __device__ constexpr int mono_ct(int beta, int i) {
+  return beta < GroupTable<ELL>::NB ? GroupTable<ELL>::mono_c(beta, i) : (i == 3 ? -2 : 0);
+}
+
+// Pair PR's two basis fields at the nodes of the R rows, built with their exponents
+// known at compile time, and the first FFT stage from registers into C.
+template <int N, int ELL, int PR>
+__device__ __forceinline__ void pair_stage0_ct(float2* C, const float2* nodes, float X, const float* __restrict__ rely,
+                                               const float* __restrict__ relz, int row0) {
   using Y = YZ<N, ELL>;
-  constexpr int E = Y::E, TPL = Y::TPL, R0 = Y::R0, R = Y::R, NB = Y::NB, LL = Y::LL, LPP = Y::LPP;
-  const int fa = 2 * pr, fb = 2 * pr + 1;
-  int aa, ab, ac, ad, ba, bb, bc, bd;
-  GroupTable<ELL>::mono(fa, aa, ab, ac, ad);
-  GroupTable<ELL>::mono(fb, ba, bb, bc, bd);
+  constexpr int E = Y::E, TPL = Y::TPL, R0 = Y::R0, R = Y::R, LL = Y::LL, LPP = Y::LPP;
+  constexpr int FA = 2 * PR, FB = 2 * PR + 1;
+  constexpr int AA = mono_ct<ELL>(FA, 0), AB = mono_ct<ELL>(FA, 1), AC = mono_ct<ELL>(FA, 2), AD = mono_ct<ELL>(FA, 3);
+  constexpr int BA = mono_ct<ELL>(FB, 0), BB = mono_ct<ELL>(FB, 1), BC = mono_ct<ELL>(FB, 2), BD = mono_ct<ELL>(FB, 3);
   const int tl = threadIdx.x % TPL;
 #pragma unroll
   for (int ps = 0; ps < Y::PASSES; ++ps) {
@@ -190,16 +197,16 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
       const float Yc = rely[row0 + row];
       const float2* nrow = nodes + row * N;
       float2* lp = C + row * LL;
-      const float Ka = ipow_rt(X, aa) * ipow_rt(Yc, ab), Kb = ipow_rt(X, ba) * ipow_rt(Yc, bb);
+      const float Ka = ipow_ct<AA>(X) * ipow_ct<AB>(Yc), Kb = ipow_ct<BA>(X) * ipow_ct<BB>(Yc);
 #pragma unroll 1
       for (int q = 0; q < E / R0; ++q) {
         float2 v[R0];
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int z = fft_in_index<N>(tl, q, r);
-          const float Zc = (ac | bc) ? relz[z] : 0.f;
+          const float Zc = (AC | BC) ? relz[z] : 0.f;
           const float2 fi = nrow[z];  // written by this thread in row_item
-          v[r] = make_float2(basis_value_rt(fi.x, fi.y, Zc, Ka, ac, ad), basis_value_rt(fi.x, fi.y, Zc, Kb, bc, bd));
+          v[r] = make_float2(basis_value_ct<AC, AD>(fi.x, fi.y, Zc, Ka), basis_value_ct<BC, BD>(fi.x, fi.y, Zc, Kb));
         }
         Dft<R0>::run(v);
         const int jq = tl + q * TPL;
@@ -214,6 +221,31 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
       }
     }
   }
+}
+
+// Run-time pair index to the compile-time build above (a uniform chain of tests).
+template <int N, int ELL, int PR = 0>
+__device__ __forceinline__ void pair_stage0(int pr, float2* C, const float2* nodes, float X,
+                                            const float* __restrict__ rely, const float* __restrict__ relz, int row0) {
+  if constexpr (PR < YZ<N, ELL>::NPAIR) {
+    if (pr == PR) pair_stage0_ct<N, ELL, PR>(C, nodes, X, rely, relz, row0);
+    else pair_stage0<N, ELL, PR + 1>(pr, C, nodes, X, rely, relz, row0);
+  }
+}
+
+// One pair of basis fields (fa = 2 pr, fb = 2 pr + 1) for the R rows of a row item:
+// fields at the nodes (first FFT stage from registers, one butterfly at a time),
+// FFT along z, then the split of the two real fields into their half spectra,
+// written to the ring slot.  C is one of two line buffers, so the split of this pair
+// can overlap the FFT of the next.
+template <int N, int ELL>
+__device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes, float X,
+                                         const float* __restrict__ rely, const float* __restrict__ relz, int row0,
+                                         const float2* tw, float2* __restrict__ zslot, int nzc) {
+  using Y = YZ<N, ELL>;
+  constexpr int TPL = Y::TPL, R = Y::R, NB = Y::NB, LL = Y::LL;
+  const int fa = 2 * pr, fb = 2 * pr + 1;
+  pair_stage0<N, ELL>(pr, C, nodes, X, rely, relz, row0);
   line_group_sync<TPL>();  // each line is written and read by its own threads
   FftRun<N, 1, false, true, R>::run(C, 1, LL, R, tw);
   __syncthreads();
