@@ -140,13 +140,12 @@ __device__ __forceinline__ int axis_tiles(int lo, int hi, int n, int tdim, int (
 // (ntiles counters), added to the global counts once per CTA at the end -- a few
 // CTAs per SM and a grid-stride loop, instead of one global atomic per (particle,
 // tile) on counters that every SM contends for.
-template <int KIND, int M, bool BIN, bool HIST = false, int NT = THREADS>
+template <int KIND, int M, bool HIST = false, int NT = THREADS>
 __global__ void __launch_bounds__(NT)
 k_particles(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
             const float* __restrict__ pw, const float* __restrict__ pnbar, int64_t n, int is_ran,
             Geom g, const float2* __restrict__ nodes, unsigned* __restrict__ tile_count,
-            unsigned* __restrict__ tile_cur, float4* __restrict__ rec,
-            double* __restrict__ sums, double alpha_cfg, int ntiles) {
+            double* __restrict__ sums, int ntiles) {
   extern __shared__ unsigned s_hist[];
   if (HIST) {
     for (int t = threadIdx.x; t < ntiles; t += NT) s_hist[t] = 0u;
@@ -155,30 +154,37 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
   // Compensated float sums per thread (Kahan), FP64 across threads.
   float s_w = 0.f, c_w = 0.f, s_w2 = 0.f, c_w2 = 0.f, s_w2n = 0.f, c_w2n = 0.f;
   unsigned bad = 0;
-  float wscale = 1.f;
-  if (BIN && is_ran) {
-    const double a = alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR];
-    wscale = (float)(-a);
-  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
-    const float x = px[idx], y = py[idx], z = pz[idx];
-    const float w = pw ? pw[idx] : 1.f;
-    int ci[3];
-    float cd[3];
-    bool ok = locate(x, 0, g, nodes, ci[0], cd[0]);
-    ok &= locate(y, 1, g, nodes, ci[1], cd[1]);
-    ok &= locate(z, 2, g, nodes, ci[2], cd[2]);
-    int tt[3][2], nt[3];
-    bool inner = true;  // every stencil node in one tile, no periodic wrap
+  // Two particles per round (the same order as one per round): their loads are issued
+  // together, so that the latencies overlap.
+  constexpr int U = 2;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * stride) {
+    float xs[U], ys[U], zs[U], ws[U], nbs[U];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int lo, hi;
-      node_range<KIND, M>(ci[a], cd[a], lo, hi);
-      nt[a] = axis_tiles(lo, hi, g.n, g.tdim[a], tt[a]);
-      inner &= nt[a] == 1 && lo >= 0 && hi < g.n;
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * stride < n ? base + u * stride : base;
+      xs[u] = px[i];
+      ys[u] = py[i];
+      zs[u] = pz[i];
+      ws[u] = pw ? pw[i] : 1.f;
+      nbs[u] = (is_ran && pnbar) ? pnbar[i] : 0.f;
     }
-    if (!BIN) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (base + u * stride >= n) break;
+      const float x = xs[u], y = ys[u], z = zs[u], w = ws[u];
+      int ci[3];
+      float cd[3];
+      bool ok = locate(x, 0, g, nodes, ci[0], cd[0]);
+      ok &= locate(y, 1, g, nodes, ci[1], cd[1]);
+      ok &= locate(z, 2, g, nodes, ci[2], cd[2]);
+      int tt[3][2], nt[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int lo, hi;
+        node_range<KIND, M>(ci[a], cd[a], lo, hi);
+        nt[a] = axis_tiles(lo, hi, g.n, g.tdim[a], tt[a]);
+      }
       bad += ok ? 0u : 1u;
       {  // Kahan updates
         float yv = w - c_w, t = s_w + yv;
@@ -186,33 +192,25 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
         yv = w * w - c_w2; t = s_w2 + yv;
         c_w2 = (t - s_w2) - yv; s_w2 = t;
         if (is_ran && pnbar) {
-          yv = w * w * pnbar[idx] - c_w2n; t = s_w2n + yv;
+          yv = w * w * nbs[u] - c_w2n; t = s_w2n + yv;
           c_w2n = (t - s_w2n) - yv; s_w2n = t;
         }
       }
-    }
-    const float weff = w * wscale;
-    for (int a = 0; a < nt[0]; ++a)
-      for (int b = 0; b < nt[1]; ++b)
-        for (int c = 0; c < nt[2]; ++c) {
-          const int tile = (tt[0][a] * g.tiles[1] + tt[1][b]) * g.tiles[2] + tt[2][c];
-          if (!BIN) {
+      for (int a = 0; a < nt[0]; ++a)
+        for (int b = 0; b < nt[1]; ++b)
+          for (int c = 0; c < nt[2]; ++c) {
+            const int tile = (tt[0][a] * g.tiles[1] + tt[1][b]) * g.tiles[2] + tt[2][c];
             if (HIST) atomicAdd(&s_hist[tile], 1u);
             else atomicAdd(&tile_count[tile], 1u);
-          } else {
-            // interior records fill the tile's list from the front, the others
-            // from the back (tile_count holds the end of each list after the scan)
-            const unsigned slot = inner ? atomicAdd(&tile_cur[tile], 1u) : atomicSub(&tile_count[tile], 1u) - 1u;
-            rec[slot] = make_float4(x, y, z, weff);
           }
-        }
+    }
   }
   if (HIST) {
     __syncthreads();
     for (int t = threadIdx.x; t < ntiles; t += NT)
       if (s_hist[t]) atomicAdd(&tile_count[t], s_hist[t]);
   }
-  if (!BIN) {
+  {
     __shared__ double red[NT / 32][4];
     double v0 = warp_sum((double)s_w - (double)c_w);
     double v1 = warp_sum((double)s_w2 - (double)c_w2);
@@ -233,6 +231,72 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
         atomicAdd(&sums[SUM_WG2], t1);
       }
       if (t3 != 0.0) atomicAdd(&sums[SUM_BAD], t3);
+    }
+  }
+}
+
+// Binning pass: one 16-byte record (position, signed weight) per tile a particle's
+// stencils touch; records whose stencils lie inside one tile (no periodic wrap) fill
+// the tile's list from the front (tile_cur), the others from the back (tile_back, the
+// end of each list after the scan).  Each thread takes U particles per round, whose
+// loads and first-tile cursor atomics are independent, so that their latencies
+// overlap (one particle per round leaves the pass waiting on each round trip).
+template <int KIND, int M, int U>
+__global__ void __launch_bounds__(THREADS)
+k_bin(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
+      const float* __restrict__ pw, int64_t n, int is_ran, Geom g, const float2* __restrict__ nodes,
+      unsigned* __restrict__ tile_back, unsigned* __restrict__ tile_cur, float4* __restrict__ rec,
+      const double* __restrict__ sums, double alpha_cfg) {
+  float wscale = 1.f;
+  if (is_ran) wscale = (float)(-(alpha_cfg >= 0.0 ? alpha_cfg : sums[SUM_WG] / sums[SUM_WR]));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * stride) {
+    float4 q[U];
+    int tt[U][3][2], nt[U][3];
+    bool inner[U], valid[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t idx = base + u * stride;
+      valid[u] = idx < n;
+      const int64_t i = valid[u] ? idx : base;
+      q[u] = make_float4(px[i], py[i], pz[i], (pw ? pw[i] : 1.f) * wscale);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int ci[3];
+      float cd[3];
+      locate(q[u].x, 0, g, nodes, ci[0], cd[0]);
+      locate(q[u].y, 1, g, nodes, ci[1], cd[1]);
+      locate(q[u].z, 2, g, nodes, ci[2], cd[2]);
+      inner[u] = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int lo, hi;
+        node_range<KIND, M>(ci[a], cd[a], lo, hi);
+        nt[u][a] = axis_tiles(lo, hi, g.n, g.tdim[a], tt[u][a]);
+        inner[u] = inner[u] && nt[u][a] == 1 && lo >= 0 && hi < g.n;
+      }
+    }
+    unsigned slot[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!valid[u]) continue;
+      const int tile = (tt[u][0][0] * g.tiles[1] + tt[u][1][0]) * g.tiles[2] + tt[u][2][0];
+      slot[u] = inner[u] ? atomicAdd(&tile_cur[tile], 1u) : atomicSub(&tile_back[tile], 1u) - 1u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (valid[u]) rec[slot[u]] = q[u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!valid[u] || inner[u]) continue;
+      for (int a = 0; a < nt[u][0]; ++a)
+        for (int b = 0; b < nt[u][1]; ++b)
+          for (int c = 0; c < nt[u][2]; ++c) {
+            if (a == 0 && b == 0 && c == 0) continue;  // the first tile is done
+            const int tile = (tt[u][0][a] * g.tiles[1] + tt[u][1][b]) * g.tiles[2] + tt[u][2][c];
+            rec[atomicSub(&tile_back[tile], 1u) - 1u] = q[u];
+          }
     }
   }
 }
@@ -639,10 +703,10 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, co
     int dev = 0, sms = 0, per = 0;
     if ((err = cudaGetDevice(&dev)) || (err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
       return err;
-    if ((err = cudaFuncSetAttribute(k_particles<KIND, M, false, true, HT>,
+    if ((err = cudaFuncSetAttribute(k_particles<KIND, M, true, HT>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hist_bytes)))
       return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_particles<KIND, M, false, true, HT>, HT,
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_particles<KIND, M, true, HT>, HT,
                                                              hist_bytes)))
       return err;
     hist_grid = std::max(1, per) * sms;
@@ -653,13 +717,11 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, co
     LaunchScope ls(p, 0);
     if (hist) {
       const int grid = (int)std::min<int64_t>(hist_grid, (k.n + HT - 1) / HT);
-      k_particles<KIND, M, false, true, HT><<<grid, HT, hist_bytes, st>>>(
-          k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr,
-          p.d_sums, p.cfg.alpha, p.ntiles);
+      k_particles<KIND, M, true, HT><<<grid, HT, hist_bytes, st>>>(k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom,
+                                                                  p.d_nodes, p.d_tile_count, p.d_sums, p.ntiles);
     } else {
-      k_particles<KIND, M, false><<<blocks(k.n), THREADS, 0, st>>>(
-          k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, nullptr, nullptr,
-          p.d_sums, p.cfg.alpha, p.ntiles);
+      k_particles<KIND, M, false><<<blocks(k.n), THREADS, 0, st>>>(k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom,
+                                                                   p.d_nodes, p.d_tile_count, p.d_sums, p.ntiles);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -672,9 +734,9 @@ cudaError_t run_assign(Plan& p, const ys_catalog& gal, const ys_catalog& ran, co
     const ys_catalog& k = *cats[c];
     if (k.n == 0) continue;
     LaunchScope ls(p, 2);
-    k_particles<KIND, M, true><<<blocks(k.n), THREADS, 0, st>>>(
-        k.x, k.y, k.z, k.w, k.nbar, k.n, c, p.geom, p.d_nodes, p.d_tile_count, p.d_tile_cur, p.d_rec,
-        p.d_sums, p.cfg.alpha, p.ntiles);
+    constexpr int U = 2;
+    k_bin<KIND, M, U><<<blocks((k.n + U - 1) / U), THREADS, 0, st>>>(
+        k.x, k.y, k.z, k.w, k.n, c, p.geom, p.d_nodes, p.d_tile_count, p.d_tile_cur, p.d_rec, p.d_sums, p.cfg.alpha);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int tvol = p.geom.tdim[0] * p.geom.tdim[1] * p.geom.tdim[2];
