@@ -554,7 +554,7 @@ ys_status ys_plan_create(const ys_config* cfg, ys_plan** out) {
   ys::set_yz_grid(p, p.yz_grid_max, ys::kRingLeadPctMax);
   p.ring_slots_cap = p.ring_slots;
   ys::set_yz_grid(p, p.yz_grid_max, 100);
-  const size_t slot = (size_t)p.nb * std::max(1, p.nzc) * n;
+  const size_t slot = (size_t)2 * ((p.nb + 1) / 2) * std::max(1, p.nzc) * n;  // field pairs interleaved
   if ((e = ys::dalloc(p, p.d_mesh, p.m * n3)) || (e = ys::dalloc(p, p.d_z, slot * p.ring_slots_cap)) ||
       (e = ys::dalloc(p, p.d_sync, (size_t)2 * p.m * n + 2)) ||
       (e = ys::dalloc(p, p.d_g, (size_t)p.m * p.ng * n * std::max(1, p.np_pad))) ||

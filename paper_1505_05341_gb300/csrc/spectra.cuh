@@ -8,7 +8,7 @@
 //                  basis fields (F, F', F r_hat^a r_hat^b r_hat^c with c <= 1) the
 //                  two real fields as one complex FFT along z, split into the two
 //                  half spectra (k_z < nzc) and written to a ring slot laid out
-//                  [field][k_z][y] (y contiguous).
+//                  [field pair][k_z][y][2] (y contiguous, the pair's fields side by side).
 //     column item  one k_z column of one plane: FFT along y of every basis field,
 //                  folded with k_y, k_z polynomial weights into the groups G_{n,p}
 //                  (power p of k_x; GroupTable); only the pencils (k_y, k_z) with
@@ -76,7 +76,7 @@ __device__ __forceinline__ float basis_value_ct(float f, float i2, float z, floa
 // Planes p = 0 .. m N - 1 (mesh j = p / N, x index p % N).  Per plane there are NZ
 // "row items" (R rows of the plane: the basis fields, complex FFTs of two real
 // fields along z, the split into the two half spectra for k_z < nzc, written to a
-// ring slot laid out [field][k_z][y]) and NY = nzc "column items" (one k_z column:
+// ring slot laid out [field pair][k_z][y][2]) and NY = nzc "column items" (one k_z column:
 // FFT along y of every basis field, the k_y, k_z polynomial fold into the k_x-power
 // groups, written for the pencils of that column).  Tickets are handed out in steps:
 // step t = row items of plane t, then column items of plane t - D.  Row items of
@@ -243,8 +243,7 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
                                          const float* __restrict__ rely, const float* __restrict__ relz, int row0,
                                          const float2* tw, float2* __restrict__ zslot, int nzc) {
   using Y = YZ<N, ELL>;
-  constexpr int TPL = Y::TPL, R = Y::R, NB = Y::NB, LL = Y::LL;
-  const int fa = 2 * pr, fb = 2 * pr + 1;
+  constexpr int TPL = Y::TPL, R = Y::R, LL = Y::LL;
   pair_stage0<N, ELL>(pr, C, nodes, X, rely, relz, row0);
   line_group_sync<TPL>();  // each line is written and read by its own threads
   FftRun<N, 1, false, true, R>::run(C, 1, LL, R, tw);
@@ -258,14 +257,14 @@ __device__ __forceinline__ void row_pair(int pr, float2* C, const float2* nodes,
   const float2* crow = C + r * LL;
   const float2* pk = crow + fft_pos<true>(kz0);
   const float2* pm = crow + fft_pos<true>(N - kz0);  // only read for k_z > 0
-  float2* za = zslot + ((size_t)fa * nzc + kz0) * N + row0 + r;
-  const size_t fstep = (size_t)nzc * N;
+  // The ring holds the two fields of a pair side by side: one 16-byte store per node.
+  float4* za = reinterpret_cast<float4*>(zslot) + ((size_t)pr * nzc + kz0) * N + row0 + r;
   for (int kz = kz0; kz < nzc; kz += KS, pk += PSTEP, pm -= PSTEP, za += (size_t)KS * N) {
     const float2 ck = STEP ? *pk : crow[fft_pos<true>(kz)];
     const float2 cm = kz ? (STEP ? *pm : crow[fft_pos<true>(N - kz)]) : ck;
-    // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i).
-    za[0] = make_float2(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y));
-    if (fb < NB) za[fstep] = make_float2(0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
+    // Two real fields a + i b: A = (C_k + C_{-k}^*)/2, B = (C_k - C_{-k}^*)/(2i) (B = 0
+    // past the last field).
+    *za = make_float4(0.5f * (ck.x + cm.x), 0.5f * (ck.y - cm.y), 0.5f * (ck.y + cm.y), -0.5f * (ck.x - cm.x));
   }
 }
 
@@ -341,29 +340,36 @@ __device__ __forceinline__ void column_item(float2* S, const float2* __restrict_
                                             const int* __restrict__ col_off, const float2* tw,
                                             float2* __restrict__ gout, int j, int ix, int np) {
   using Y = YZ<N, ELL>;
-  constexpr int NB = Y::NB, E = Y::E, TPL = Y::TPL, R0 = Y::R0, LL = Y::LL, LPP = Y::LPP;
+  constexpr int NB = Y::NB, NP = Y::NPAIR, E = Y::E, TPL = Y::TPL, R0 = Y::R0, LL = Y::LL, LPP = Y::LPP;
   const int tl = threadIdx.x % TPL;
-  for (int base = 0; base < NB; base += LPP) {
-    const int f = base + threadIdx.x / TPL;
-    if (f < NB) {
-      const float2* line = zs + ((size_t)f * nzc + kz) * N;
-      float2 v[E];
+  // One ring line holds a pair of fields (16 bytes per node): a thread group loads
+  // both and runs the first FFT stage of each.
+  for (int base = 0; base < NP; base += LPP) {
+    const int pr = base + threadIdx.x / TPL;
+    if (pr < NP) {
+      const float4* line = reinterpret_cast<const float4*>(zs) + ((size_t)pr * nzc + kz) * N;
+      float2 va[E], vb[E];
 #pragma unroll
       for (int q = 0; q < E / R0; ++q)
 #pragma unroll
-        for (int r = 0; r < R0; ++r) v[q * R0 + r] = __ldcg(line + fft_in_index<N>(tl, q, r));
-      fft_stage0_regs<N, true>(v, S + f * LL, 1, tl);
+        for (int r = 0; r < R0; ++r) {
+          const float4 t = __ldcg(line + fft_in_index<N>(tl, q, r));
+          va[q * R0 + r] = make_float2(t.x, t.y);
+          vb[q * R0 + r] = make_float2(t.z, t.w);
+        }
+      fft_stage0_regs<N, true>(va, S + 2 * pr * LL, 1, tl);
+      if (2 * pr + 1 < NB) fft_stage0_regs<N, true>(vb, S + (2 * pr + 1) * LL, 1, tl);
     }
   }
-  line_group_sync<TPL>();  // each line is written and read by its own threads
+  __syncthreads();  // every ring load is done; lines 2 pr, 2 pr + 1 came from pair pr's threads
   // The ring lines of this column are dead once read: drop them from L2 without a
   // write-back (the slot is rewritten only after this item's completion is
-  // released).  Each line is N * 8 bytes, a whole number of 128-byte lines.
-  for (int base = 0; base < NB; base += LPP) {
-    const int f = base + threadIdx.x / TPL;
-    if (f < NB && tl < N / 16) {
-      const float2* line = zs + ((size_t)f * nzc + kz) * N;
-      asm volatile("discard.global.L2 [%0], 128;" ::"l"(line + tl * 16) : "memory");
+  // released).  Each line is N * 16 bytes, a whole number of 128-byte lines.
+  for (int base = 0; base < NP; base += LPP) {
+    const int pr = base + threadIdx.x / TPL;
+    if (pr < NP) {
+      const float4* line = reinterpret_cast<const float4*>(zs) + ((size_t)pr * nzc + kz) * N;
+      for (int c = tl; c < N / 8; c += TPL) asm volatile("discard.global.L2 [%0], 128;" ::"l"(line + c * 8) : "memory");
     }
   }
   FftRun<N, 1, false, true, NB>::run(S, 1, LL, NB, tw);
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid
     const int item = gitem - (l > 0 ? pm.end[l - 1] : 0);
     const int NY = prm.nzc, IPS = NZ + NY;
     const int mN = prm.m * N;
-    const size_t slot_elems = (size_t)Y::NB * prm.nzc * N;
+    const size_t slot_elems = (size_t)2 * Y::NPAIR * prm.nzc * N;  // float2 units, field pairs interleaved
     const int step = item / IPS, sub = item - step * IPS;
     if (sub < NZ) {
       const int p = step;  // row item of plane p
