@@ -15,7 +15,10 @@ them in a random order as concurrent atomics would, and checks that:
 * plain float accumulation of the same terms moves P_4 by more than the 1e-4 bar
   in some shell (the failure the pair removes), and depends on the order;
 * with FP64-quality sums, the float32 rounding of the transforms alone keeps every
-  P_l within 5e-5 of the oracle -- the part of the budget left for the FFTs.
+  P_l within 5e-5 of the oracle -- the part of the budget left for the FFTs;
+* the same holds when runs of equal shells among neighbouring modes are first summed
+  across lanes with error-carrying adds (the x stage's warp scan) and only then added
+  to the bins.
 """
 import numpy as np
 
@@ -96,3 +99,59 @@ def test_compensated_float_bins_equal_fp64_accumulation():
     assert plain_worst[0] != plain_worst[1]
     # the float32 transforms with FP64-quality sums stay inside half the bar
     assert max(_worst(ref, exact, nm, has)) < 5e-5
+
+
+def _two_sum_err(a, b):
+    s = f32(a + b)
+    bb = f32(s - a)
+    return f32(f32(a - f32(s - bb)) + f32(b - bb))
+
+
+def _run_reduced_bins(b, v, nb, chunks, order):
+    """The x stage's order of operations: the lanes of one pencil (here a chunk of
+    neighbouring modes) first sum each run of equal shells in the segmented suffix
+    scan's tree order (offsets 1, 2, 4 within the chunk), carrying every add's exact
+    error; the run's first lane then adds the sum to the bin and the carried error
+    plus the add's own error to the companion bin."""
+    s = np.zeros(nb, f32)
+    c = np.zeros(nb, f32)
+    for ci in order:
+        idx = chunks[ci]
+        key = b[idx]
+        L = idx.size
+        val = v[idx].astype(f32).copy()
+        cmp = np.zeros(L, f32)
+        end = np.array([j == L - 1 or key[j + 1] != key[j] for j in range(L)])
+        d = 1
+        while d < L:
+            vn, cn, en = val.copy(), cmp.copy(), end.copy()
+            for j in range(L):
+                if not end[j]:
+                    cmp[j] = f32(cmp[j] + f32(cn[j + d] + _two_sum_err(val[j], vn[j + d])))
+                    val[j] = f32(val[j] + vn[j + d])
+                    end[j] = en[j + d]
+            d *= 2
+        for j in range(L):
+            k = key[j]
+            if k >= 0 and (j == 0 or key[j - 1] != k):
+                old = s[k]
+                s[k] = f32(old + val[j])
+                c[k] = f32(c[k] + f32(cmp[j] + _two_sum_err(old, val[j])))
+    return s.astype(np.float64) + c.astype(np.float64)
+
+
+def test_run_reduced_compensated_bins_equal_fp64_accumulation():
+    ref, bidx, w, nb, terms = _case(93)
+    b = bidx.ravel()
+    nchunk = b.size // 8
+    chunks = [np.arange(8 * i, 8 * i + 8) for i in range(nchunk)]  # neighbouring modes
+    exact = [bin_sums(t.astype(np.float64).ravel()[:8 * nchunk], b[:8 * nchunk], np.ones(8 * nchunk), nb)
+             for t in terms]
+    scale = [bin_sums(np.abs(t.astype(np.float64)).ravel()[:8 * nchunk], b[:8 * nchunk], np.ones(8 * nchunk), nb)
+             for t in terms]
+    multi = sum(1 for ch in chunks if np.unique(b[ch][b[ch] >= 0]).size > 1)
+    assert multi > 0  # some chunks hold more than one run
+    order = np.random.default_rng(1).permutation(nchunk)
+    for t, e, sc in zip(terms, exact, scale):
+        got = _run_reduced_bins(b, t.ravel(), nb, chunks, order)
+        assert np.all(np.abs(got - e) <= 1e-12 * sc + 1e-30)
