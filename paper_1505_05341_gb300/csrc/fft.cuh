@@ -250,10 +250,19 @@ __device__ __forceinline__ void fft_stage(float2* buf, int es, int ls, int nl_rt
   }
 }
 
+// Padded buffers of interleaved lines (x stage: element x of line p at x P + p):
+// PADP > 0 inserts PADP elements after every 8 PADP, so that the stores of a radix-8
+// first stage, 8 P apart across a warp, land on distinct bank pairs.
+template <int PADP>
+__host__ __device__ constexpr int lf_pad(int i) {
+  return PADP > 0 ? i + (i / (8 * PADP)) * PADP : i;
+}
+
 // Out-of-place stage: reads the lines from src and writes them to dst (no barrier
 // inside; the caller synchronises before dst is read).  With two buffers a stage
-// needs one barrier instead of the two an in-place stage needs.
-template <int N, int S, bool LF>
+// needs one barrier instead of the two an in-place stage needs.  PIN / POUT: the
+// padding (lf_pad) of src / dst.
+template <int N, int S, bool LF, int PIN = 0, int POUT = 0>
 __device__ __forceinline__ void fft_stage_oop(const float2* src, float2* dst, int es, int ls, int nl,
                                               const float2* tw) {
   constexpr int R = fft_radix(N, S);
@@ -272,14 +281,13 @@ __device__ __forceinline__ void fft_stage_oop(const float2* src, float2* dst, in
   for (int base_line = 0; base_line < nl; base_line += lpp) {
     const int line = base_line + lane_line;
     if (!in_pass || line >= nl) continue;
-    const float2* lp = src + line * ls;
-    float2* lq = dst + line * ls;
+    const int lo = line * ls;
     float2 v[E];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int j = tl + q * TPL;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = lp[(j + r * STRIDE) * es];
+      for (int r = 0; r < R; ++r) v[q * R + r] = src[lf_pad<PIN>(lo + (j + r * STRIDE) * es)];
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
@@ -293,23 +301,23 @@ __device__ __forceinline__ void fft_stage_oop(const float2* src, float2* dst, in
       Dft<R>::run(&v[q * R]);
       const int outb = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) lq[(outb + r * NS) * es] = v[q * R + r];
+      for (int r = 0; r < R; ++r) dst[lf_pad<POUT>(lo + (outb + r * NS) * es)] = v[q * R + r];
     }
   }
 }
 
 // Stages [S, END) alternating between buffers a and b (CTA-wide barrier after each);
-// the result sits in a when END - S is even, else in b.
-template <int N, int S, int END, bool Done = (S >= END)>
+// the result sits in a when END - S is even, else in b.  PA / PB: their padding.
+template <int N, int S, int END, int PA = 0, int PB = 0, bool Done = (S >= END)>
 struct FftPingPong {
   __device__ static __forceinline__ void run(float2* a, float2* b, int es, int ls, int nl, const float2* tw) {
-    fft_stage_oop<N, S, true>(a, b, es, ls, nl, tw);
+    fft_stage_oop<N, S, true, PA, PB>(a, b, es, ls, nl, tw);
     __syncthreads();
-    FftPingPong<N, S + 1, END>::run(b, a, es, ls, nl, tw);
+    FftPingPong<N, S + 1, END, PB, PA>::run(b, a, es, ls, nl, tw);
   }
 };
-template <int N, int S, int END>
-struct FftPingPong<N, S, END, true> {
+template <int N, int S, int END, int PA, int PB>
+struct FftPingPong<N, S, END, PA, PB, true> {
   __device__ static __forceinline__ void run(float2*, float2*, int, int, int, const float2*) {}
 };
 
@@ -327,10 +335,11 @@ struct FftRun<N, S, LF, PAD, NL, true> {
 };
 
 // Last stage into registers: stages 0 .. S-2 must already have run on the lines.
-// Each thread loads its butterfly inputs from the line lp, applies twiddles and the
-// DFT, and keeps the outputs: v[q * R + r] is element (tl + q * TPL) + r * (N / R).
-template <int N, bool LF, bool PAD>
-__device__ __forceinline__ void fft_last_stage_regs(const float2* lp, int es, int tl, const float2* tw,
+// Each thread loads its butterfly inputs from line `line` of buf (element i at
+// line + i es, padded by lf_pad<PADL>), applies twiddles and the DFT, and keeps the
+// outputs: v[q * R + r] is element (tl + q * TPL) + r * (N / R).
+template <int N, bool LF, bool PAD, int PADL = 0>
+__device__ __forceinline__ void fft_last_stage_regs(const float2* buf, int line, int es, int tl, const float2* tw,
                                                     float2 (&v)[LF ? fft_elems_lf(N) : fft_elems(N)]) {
   constexpr int S = fft_nstages(N) - 1;
   constexpr int R = fft_radix(N, S);
@@ -344,7 +353,7 @@ __device__ __forceinline__ void fft_last_stage_regs(const float2* lp, int es, in
   for (int q = 0; q < NB; ++q) {
     const int j = tl + q * TPL;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[q * R + r] = lp[fft_pos<PAD>(j + r * STRIDE) * es];
+    for (int r = 0; r < R; ++r) v[q * R + r] = buf[lf_pad<PADL>(line + fft_pos<PAD>(j + r * STRIDE) * es)];
   }
 #pragma unroll
   for (int q = 0; q < NB; ++q) {

@@ -568,6 +568,9 @@ struct XCombine {
   static constexpr int BOXES = N / BOX_ROWS;
   static_assert(BOXES * BOX_ROWS == N, "boxes must tile the x axis");
   static constexpr unsigned TILE_BYTES = (unsigned)(N * P * sizeof(float2));
+  // work buffer padded (lf_pad) where the first stage is radix 8
+  static constexpr int PADW = fft_radix(N, 0) == 8 ? P : 0;
+  static constexpr int WK_ELEMS = lf_pad<PADW>(N * P);
   static constexpr int RL = fft_radix(N, fft_nstages(N) - 1);  // last radix
   // resident CTAs per SM the register budget is set for (3 x 256 threads at 256^3, 512^3)
   static constexpr int MIN_BLOCKS = ((N == 256 || N == 512) && ELL <= 4 && THREADS == 256) ? 3 : 1;
@@ -579,7 +582,7 @@ struct XCombine {
   // atomics are served one after another); with fewer copies warp w adds into copy
   // w mod nwb.
   static size_t smem(int nbins, int nwb) {
-    size_t b = 3 * (size_t)TILE_BYTES;                       // two tile buffers and a work buffer
+    size_t b = 2 * (size_t)TILE_BYTES + sizeof(float2) * WK_ELEMS;  // two tile buffers and a work buffer
     b += sizeof(float2) * 2 * N + sizeof(float) * N;         // twiddles, phases, windows
     b += sizeof(float) * 2 * nwb * SLOTS * nbins;            // float bins and their error terms
     return b + 128;                                          // alignment slack
@@ -604,8 +607,8 @@ k_x_combine(const __grid_constant__ XMulti pm, int np_pad, const short2* __restr
   __shared__ int s_fail;
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   float2* T0 = reinterpret_cast<float2*>(base);
-  float2* Wk = T0 + 2 * N * P;  // second buffer of the out-of-place stages
-  float2* tw = Wk + N * P;
+  float2* Wk = T0 + 2 * N * P;  // second buffer of the out-of-place stages (padded)
+  float2* tw = Wk + XC::WK_ELEMS;
   float2* phs = tw + N;
   float* invw = reinterpret_cast<float*>(phs + N);
   constexpr int SLOTS = XC::SLOTS;
@@ -678,10 +681,11 @@ k_x_combine(const __grid_constant__ XMulti pm, int np_pad, const short2* __restr
     }
     float2* Tb = T0 + (s & 1) * N * P;
     constexpr int SM_STAGES = fft_nstages(N) - 1;  // stages through shared memory
-    FftPingPong<N, 0, SM_STAGES>::run(Tb, Wk, P, 1, P, tw);
+    FftPingPong<N, 0, SM_STAGES, 0, XC::PADW>::run(Tb, Wk, P, 1, P, tw);
     const float2* Tf = (SM_STAGES % 2 == 0) ? Tb : Wk;
+    constexpr int PADF = (SM_STAGES % 2 == 0) ? 0 : XC::PADW;
     float2 v[E];
-    fft_last_stage_regs<N, true, false>(Tf + p, P, tl, tw, v);
+    fft_last_stage_regs<N, true, false, PADF>(Tf, p, P, tl, tw, v);
     const int first = group_first(gi);
     const int pw = gi - first;  // power of k_x
 #pragma unroll
