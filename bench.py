@@ -190,7 +190,7 @@ def fft_flops(cls, n, m, n_pencils, nzc, pairs=8, fields=16, groups=9):
 # dram__bytes_{read,write}.sum capture; profiles/dram_traffic_shell512_tsc_il.md).
 # Remove an entry when its kernel changes.  particle_count and particle_bin: the mean
 # of the galaxy and random launches.
-TRAFFIC = {"yz_stage": 7.83e9, "x_combine": 6.09e9, "tile_deposit": 2.50e9, "particle_bin": 1.23e9,
+TRAFFIC = {"yz_stage": 8.86e9, "x_combine": 5.77e9, "tile_deposit": 2.50e9, "particle_bin": 1.26e9,
            "particle_count": 0.58e9}
 
 
