@@ -155,7 +155,7 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
   float s_w = 0.f, c_w = 0.f, s_w2 = 0.f, c_w2 = 0.f, s_w2n = 0.f, c_w2n = 0.f;
   unsigned bad = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // Two particles per round (the same order as one per round): their loads are issued
+  // Two particles per iteration (the same order as one per iteration): their loads are issued
   // together, so that the latencies overlap.
   constexpr int U = 2;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += U * stride) {
@@ -238,9 +238,9 @@ k_particles(const float* __restrict__ px, const float* __restrict__ py, const fl
 // Binning pass: one 16-byte record (position, signed weight) per tile a particle's
 // stencils touch; records whose stencils lie inside one tile (no periodic wrap) fill
 // the tile's list from the front (tile_cur), the others from the back (tile_back, the
-// end of each list after the scan).  Each thread takes U particles per round, whose
+// end of each list after the scan).  Each thread takes U particles per iteration, whose
 // loads and first-tile cursor atomics are independent, so that their latencies
-// overlap (one particle per round leaves the pass waiting on each round trip).
+// overlap (one particle per iteration leaves the pass waiting on each memory round trip).
 template <int KIND, int M, int U>
 __global__ void __launch_bounds__(THREADS)
 k_bin(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
