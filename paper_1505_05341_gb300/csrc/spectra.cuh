@@ -282,7 +282,8 @@ __device__ __forceinline__ float recip_nr(float x) {
 template <int N, int ELL>
 __device__ __forceinline__ void row_item(float2* work, float2* nodes, const float* __restrict__ plane, float X,
                                          const float* __restrict__ rely, const float* __restrict__ relz, int row0,
-                                         const float2* tw, float2* __restrict__ zslot, int nzc) {
+                                         const float2* tw, float2* __restrict__ zslot, int nzc, int* ticket,
+                                         int& next) {
   using Y = YZ<N, ELL>;
   constexpr int R = Y::R, LL = Y::LL, E = Y::E, TPL = Y::TPL, R0 = Y::R0, LPP = Y::LPP;
   const int tl = threadIdx.x % TPL;
@@ -306,8 +307,10 @@ __device__ __forceinline__ void row_item(float2* work, float2* nodes, const floa
     }
   }
 #pragma unroll 1
-  for (int pr = 0; pr < Y::NPAIR; ++pr)
+  for (int pr = 0; pr < Y::NPAIR; ++pr) {
+    if (pr == Y::NPAIR - 1 && threadIdx.x == 0) next = atomicAdd(ticket, 1);  // see k_yz
     row_pair<N, ELL>(pr, work + (pr & 1) * R * LL, nodes, X, rely, relz, row0, tw, zslot, nzc);
+  }
 }
 
 template <int N, int ELL>
@@ -338,7 +341,7 @@ __device__ __forceinline__ void column_fold(const float2* S, int kz, const int* 
 template <int N, int ELL>
 __device__ __forceinline__ void column_item(float2* S, const float2* __restrict__ zs, int nzc, int kz,
                                             const int* __restrict__ col_off, const float2* tw,
-                                            float2* __restrict__ gout, int j, int ix, int np) {
+                                            float2* __restrict__ gout, int j, int ix, int np, int* ticket, int& next) {
   using Y = YZ<N, ELL>;
   constexpr int NB = Y::NB, NP = Y::NPAIR, E = Y::E, TPL = Y::TPL, R0 = Y::R0, LL = Y::LL, LPP = Y::LPP;
   const int tl = threadIdx.x % TPL;
@@ -374,6 +377,7 @@ __device__ __forceinline__ void column_item(float2* S, const float2* __restrict_
   }
   FftRun<N, 1, false, true, NB>::run(S, 1, LL, NB, tw);
   __syncthreads();
+  if (threadIdx.x == 0) next = atomicAdd(ticket, 1);  // see k_yz
   column_fold<N, ELL>(S, kz, col_off, gout, j, ix, np);
 }
 
@@ -398,14 +402,17 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid
   const int NZ = N / R;
   const int total = pm.end[pm.nlanes - 1];
   const size_t n3 = (size_t)N * N * N;
+  if (threadIdx.x == 0) s_item = atomicAdd(pm.ticket, 1);
   __syncthreads();
+  int gitem = s_item;
   for (;;) {
-    // One ticket at a time: a claimed item must start at once, since later items
-    // may depend on it.
-    if (threadIdx.x == 0) s_item = atomicAdd(pm.ticket, 1);
-    __syncthreads();
-    const int gitem = s_item;
     if (gitem >= total) break;
+    // Thread 0 claims the next ticket shortly before this item ends (before the last
+    // field pair of a row item, before the fold of a column item), so that the
+    // atomic's round trip overlaps the item's tail.  A claimed item starts that
+    // little later; claiming a whole item ahead delayed the items waiting on it too
+    // much.  Items wait only on items of earlier tickets, so the list cannot deadlock.
+    int next = -1;
     {  // L2 prefetch of the mesh rows of the row item one grid of tickets ahead
       const int ahead = gitem + (int)gridDim.x;
       if (ahead < total && threadIdx.x < R * N / 32) {
@@ -439,7 +446,7 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid
         const int j = p / N, ix = p - j * N;
         const float* rel = prm.rel + (size_t)j * 3 * N;
         row_item<N, ELL>(work, nodes, prm.mesh + j * n3 + (size_t)ix * N * N, rel[ix], rel + N, rel + 2 * N, sub * R,
-                         tw, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc);
+                         tw, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc, pm.ticket, next);
         if (p != prm.skip_plane) signal_release(prm.done_z + p);
         else __syncthreads();  // withheld: the column items of plane p wait until their limit
       }
@@ -451,11 +458,14 @@ __global__ void __launch_bounds__(256, YZ<N, ELL>::MIN_BLOCKS) k_yz(const __grid
         if (!s_ok) break;
         const int j = p / N, ix = p - j * N;
         column_item<N, ELL>(work, prm.ring + (size_t)(p % prm.S) * slot_elems, prm.nzc, sub - NZ, prm.col_off, tw,
-                            prm.gout, j, ix, prm.np);
+                            prm.gout, j, ix, prm.np, pm.ticket, next);
         signal_release(prm.done_y + p);
       }
     }
-    __syncthreads();  // s_item is rewritten at the top of the next round
+    __syncthreads();  // every thread is past this item before s_item changes
+    if (threadIdx.x == 0) s_item = next >= 0 ? next : atomicAdd(pm.ticket, 1);
+    __syncthreads();
+    gitem = s_item;
   }
 }
 
