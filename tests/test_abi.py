@@ -64,6 +64,7 @@ def test_null_arguments():
     assert lib.ys_plan_create(None, None) == ystat.YS_ERR_ARG
     assert lib.ys_assign(None, None, None) == ystat.YS_ERR_ARG
     assert lib.ys_measure_multipoles(None, None) == ystat.YS_ERR_ARG
+    assert lib.ys_plan_copy_mesh(None, None, 0) == ystat.YS_ERR_ARG
     assert lib.ys_plan_destroy(None) == ystat.YS_OK
     assert lib.ys_plan_device_bytes(None) == 0
 
