@@ -2,7 +2,7 @@
 (host-side code only): a small driver built with -fsanitize=address,undefined runs
 every kernel, with and without the half-cell shift, on particles that include the box
 faces, points a rounding step below the far face, and points outside the box (indices
-wrap).  Any sanitizer report aborts the driver; its mesh must equal the numpy deposit."""
+wrap).  Any sanitizer report aborts the test program; its mesh must equal the numpy deposit."""
 import os
 import shutil
 import subprocess
